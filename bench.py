@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the 3D degridding hot path; prints one JSON line.
+
+A step is one degrid_execute over the whole workload: 64 subgrids of
+512 x 512 x 4 complex64 samples with 250,000 visibilities each on random
+lines (16M visibilities), Kaiser-Bessel G_uv (support 8, oversampling 16384)
+and G_w (support 4, oversampling 128).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MB write, outside the step events)
+before every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank degrids its own copy of the workload on its
+own GPU (independent subgrid shards, no collective on the data path); the
+step time is the maximum over ranks and `value` counts all ranks' work.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "degridded visibilities/s on 1 GB300: FP32 vs BF16/FP16 subgrids at stated error"
+UNIT = "visibilities/s"
+WORKLOAD = "lines64_250k"
+WORKLOAD_DESC = ("64 subgrids of 512x512x4 complex64 (i.i.d. complex Gaussian), 250,000 "
+                 "visibilities per subgrid on a random line each (16,000,000 total); "
+                 "separable Kaiser-Bessel G_uv support 8 oversampling 16384, G_w support 4 "
+                 "oversampling 128")
+FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 4 flop)
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--sweep-steps", type=int, default=500)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(torch, dev) -> str:
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return str(dev.index)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2102_12739_gb300 import synth
+    g_uv, g_w = synth.default_tables()
+    w = synth.workload(WORKLOAD)
+    # one step = the oracle over one subgrid's 250,000 visibilities
+    s = 0
+    lo, hi = int(w.vis_offsets[s]), int(w.vis_offsets[s + 1])
+    sub = w.subgrid(s)[None].astype(np.complex128)
+    uvw = w.uvw[lo:hi]
+    offs = np.array([0, hi - lo])
+    for _ in range(args.warmup):
+        oracle.degrid(g_uv, g_w, sub, uvw, offs)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.degrid(g_uv, g_w, sub, uvw, offs)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * (hi - lo) / total
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC,
+                   "step": "FP64 CPU oracle over subgrid 0 (250,000 visibilities)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "subgrid 0 of the workload, 250,000 visibilities per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(w, g_uv, g_w):
+    """The FP64 oracle, as it stands, over the whole workload once."""
+    import oracle
+    sub = w.subgrids().astype(np.complex128)
+    t0 = time.perf_counter()
+    _, bad = oracle.degrid(g_uv, g_w, sub, w.uvw, w.vis_offsets)
+    dt = time.perf_counter() - t0
+    return {"value": w.n_vis / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"the whole workload once ({w.n_vis} visibilities, {dt:.2f} s)"}
+
+
+def sampled_error(plan_out, w, g_uv, g_w, subgrids_np, n_subgrids=4, per=2000, seed=0):
+    """Relative L2 error of device output vs the FP64 oracle on sampled visibilities."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    subs = np.linspace(0, w.n_subgrids - 1, n_subgrids).astype(int)
+    idx, counts = [], []
+    for s in subs:
+        lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
+        pick = np.unique(rng.integers(lo, hi, per))
+        idx.append(pick)
+        counts.append(len(pick))
+    idx = np.concatenate(idx)
+    sub = np.stack([subgrids_np[s] for s in subs]).astype(np.complex128)
+    ref, _ = oracle.degrid(g_uv, g_w, sub, w.uvw[idx], np.concatenate([[0], np.cumsum(counts)]))
+    got = plan_out[idx]
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), float(np.max(np.abs(got - ref)))
+
+
+def time_steps(torch, plan, call, steps, flush_buf, stream):
+    """Run `steps` calls with an L2 flush before each; return per-step event
+    times (ms) and per-launch main-kernel times (ms)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush_buf.zero_()
+        ev[i][0].record(stream)
+        call()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = plan.kernel_times_ms(steps)
+    return step_ms, kern_ms
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2102_12739_gb300 as dg
+    from paper_2102_12739_gb300 import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peaks, peaks_src = measured_peaks()
+
+    g_uv, g_w = synth.default_tables()
+    w = synth.workload(WORKLOAD)
+    sub_np = w.subgrids()
+    sub = torch.from_numpy(sub_np).to(dev)
+    uvw = torch.from_numpy(w.uvw).to(dev)
+    offs = torch.from_numpy(w.vis_offsets).to(dev)
+    out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    plan = dg.DegridPlan(device=dev)
+    plan.enable_timing(max(args.steps, args.sweep_steps, 16))
+
+    def step():
+        plan.degrid(sub, uvw, offs, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+
+    sampler = ClockSampler(gpu_query_id(torch, dev)) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    wall0 = time.perf_counter()
+    step_ms, kern_ms = time_steps(torch, plan, step, args.steps, flush, stream)
+    wall = time.perf_counter() - wall0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+
+    mean_step = sum(step_ms) / len(step_ms)
+    mean_kern = sum(kern_ms) / len(kern_ms)
+    if world > 1:
+        t = torch.tensor([mean_step, mean_kern], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mean_step, mean_kern = float(t[0]), float(t[1])
+    value = world * w.n_vis / (mean_step * 1e-3)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    out_np = out.cpu().numpy()
+    err_c64 = sampled_error(out_np, w, g_uv, g_w, sub_np)
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = w.n_vis * FLOP_PER_VIS / (mean_kern * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "degrid_kernel<DG_C64>",
+                "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
+                               f"lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
+                "kernel_ms": mean_kern}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "n_vis": w.n_vis,
+                   "subgrid_storage": "complex64",
+                   "l2": "flushed before every step (256 MB write outside the step events)",
+                   "parallelism": "independent subgrid shards, one per GPU" if world > 1 else "1 GPU",
+                   "tuning": plan.tuning(), "peaks": peaks_src},
+        "roofline": roofline,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "accuracy": {"rel_l2_vs_oracle": err_c64[0], "max_abs_vs_oracle": err_c64[1],
+                     "sample": "4 subgrids x 2000 sampled visibilities"},
+        "wall_s_timed_region": wall,
+    }
+
+    if not args.no_sweep:
+        sweep = {"c64": {"value": value, "kernel_ms": mean_kern, "rel_l2": err_c64[0]}}
+        for dt in ("f16", "bf16"):
+            codes, scale = dg.pack_subgrids(sub, dt)
+            with dg.DegridPlan(dtype=dt, device=dev) as p2:
+                p2.enable_timing(args.sweep_steps)
+                o2 = torch.empty_like(out)
+
+                def step2():
+                    p2.degrid(codes, uvw, offs, scale=scale, out=o2)
+                for _ in range(max(args.warmup, 3)):
+                    step2()
+                s_ms, k_ms = time_steps(torch, p2, step2, args.sweep_steps, flush, stream)
+                e = sampled_error(o2.cpu().numpy(), w, g_uv, g_w, sub_np)
+            ms = sum(s_ms) / len(s_ms)
+            sweep[dt] = {"value": w.n_vis / (ms * 1e-3), "kernel_ms": sum(k_ms) / len(k_ms),
+                         "rel_l2": e[0], "max_abs": e[1]}
+            del codes, scale
+        line["precision_sweep"] = sweep
+
+    if not args.no_e2e:
+        h_sub = torch.empty(sub.shape, dtype=sub.dtype, pin_memory=True)
+        h_sub.copy_(torch.from_numpy(sub_np))
+        h_uvw = torch.empty(uvw.shape, dtype=uvw.dtype, pin_memory=True)
+        h_uvw.copy_(torch.from_numpy(w.uvw))
+        h_offs = torch.from_numpy(w.vis_offsets).pin_memory()
+        h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        e2e_t = []
+        for i in range(args.e2e_steps + 2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sub.copy_(h_sub, non_blocking=True)
+            uvw.copy_(h_uvw, non_blocking=True)
+            offs.copy_(h_offs, non_blocking=True)
+            plan.degrid(sub, uvw, offs, out=out)
+            h_out.copy_(out, non_blocking=True)
+            stream.synchronize()
+            if i >= 2:
+                e2e_t.append(time.perf_counter() - t0)
+        bi = h_sub.numel() * h_sub.element_size() + h_uvw.numel() * 8 + h_offs.numel() * 8
+        bo = h_out.numel() * h_out.element_size()
+        line["e2e"] = {"value": w.n_vis / statistics.median(e2e_t), "unit": UNIT,
+                       "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
+                       "path": "pinned host -> device copies, degrid_execute, device -> pinned host"}
+
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, g_uv, g_w)
+
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

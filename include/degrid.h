@@ -1,0 +1,220 @@
+/*
+ * degrid.h -- C ABI of the GB300 (sm_103a) 3D degridding library.
+ *
+ * The operation is the one stated in arXiv:2102.12739, Section
+ * "Implementation": given precomputed oversampled gridding convolution
+ * functions G_uv (support 8 x 8) and G_w (support 4), a stack of S subgrids
+ * of 512 x 512 x 4 regularly sampled visibilities and, for every subgrid, a
+ * list of visibility coordinates [u, v, w], compute for every visibility the
+ * subgrid point g = [x, y, z] where its footprint starts and the rows of the
+ * GCFs to use, then the sum of the 8 x 8 x 4 footprint samples weighted by
+ * G_uv times G_w.  The adjoint (gridding) scatters visibilities back with the
+ * same weights.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Subgrid stack: C-order [S][ny][nx][nz] complex values (y <-> v,
+ *    x <-> u, z <-> w).  Complex values are interleaved (re, im).
+ *  - Coordinates: double [N][3] = (u, v, w) in subgrid pixel units with the
+ *    origin at element (0, 0, 0).  The lists of consecutive subgrids are
+ *    concatenated; vis_offsets [S + 1] (int64, non-decreasing, first 0, last
+ *    N) delimits them.
+ *  - Snapping (the paper leaves it open; this is the library's definition):
+ *    per axis with support W and oversampling O (a power of two),
+ *    p = rint(q * O) with ties to even, i = floor(p / O), f = p - i * O,
+ *    start = i - W/2 + 1.  A visibility is valid when q is finite,
+ *    |q * O| < 2^62 and 0 <= start <= n - W on every axis.  Invalid
+ *    visibilities produce 0 (and nothing in the adjoint) and are counted.
+ *  - GCF tables: row f, column k holds the kernel value at grid offset
+ *    (k - W/2 + 1) - f/O; G_uv is separable, G_uv(a, b) = g_uv[fu][a] *
+ *    g_uv[fv][b].
+ *  - Device pointers are owned by the caller (a torch tensor's data_ptr() can
+ *    be passed directly) and must stay valid until the stream reaches the
+ *    work.  Every execute call is asynchronous on the given stream
+ *    (cudaStream_t passed as void*, NULL = legacy default stream) and does
+ *    not synchronise.
+ *  - Argument errors are detected on the host and returned before anything
+ *    is enqueued.  Data-dependent conditions (out-of-bounds coordinates,
+ *    malformed vis_offsets) are recorded on the device and reported by
+ *    degrid_get_status.  No entry point traps or asserts on the device.
+ *  - A plan is bound to one device and is not thread-safe: calls on one plan
+ *    must not run concurrently from several host threads.
+ */
+#ifndef DEGRID_H
+#define DEGRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct degrid_plan *degrid_plan_t;
+
+typedef enum {
+    DG_OK = 0,
+    DG_ERR_ARG = 1,            /* invalid argument (NULL pointer, bad size...) */
+    DG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    DG_ERR_OOM = 3,            /* a device allocation failed */
+    DG_ERR_DTYPE = 4,          /* storage type not supported / scale missing */
+    DG_ERR_OFFSETS = 5,        /* vis_offsets malformed (found on the device) */
+    DG_ERR_UNSUPPORTED = 6     /* GCF support / subgrid shape not supported */
+} dg_status;
+
+/* Subgrid storage: complex64, or FP16 / BF16 (re, im) pairs with one FP32
+ * scale per subgrid (value = code * scale). */
+typedef enum {
+    DG_C64 = 0,
+    DG_C32_F16 = 1,
+    DG_C32_BF16 = 2
+} dg_dtype;
+
+/* Human-readable name of a status code (static string). */
+const char *degrid_status_string(dg_status status);
+
+/* Library version string (static). */
+const char *degrid_version(void);
+
+/*
+ * Create a plan (Section "Implementation": the precomputed oversampled GCFs
+ * and the 512 x 512 x 4 subgrid shape are the fixed inputs of the method).
+ *   out            receives the plan handle (set to NULL on failure)
+ *   nx, ny, nz     subgrid extent; layout [S][ny][nx][nz]; nz >= w_support,
+ *                  ny * nx * nz < 2^31
+ *   g_uv           HOST double [uv_oversample][uv_support], copied (and
+ *                  rounded to FP32) to the device; the caller keeps it
+ *   uv_support     must be 8 (the paper's 8 x 8 footprint)
+ *   uv_oversample  power of two, 1 .. 2^20
+ *   g_w            HOST double [w_oversample][w_support], copied likewise
+ *   w_support      must be 4
+ *   w_oversample   power of two, 1 .. 2^20
+ *   dtype          storage type of the subgrids passed to degrid_execute
+ *   device         CUDA device ordinal; it is made current for the call
+ * Returns DG_OK, DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM or DG_ERR_CUDA.
+ */
+dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz,
+                             const double *g_uv, int uv_support, int uv_oversample,
+                             const double *g_w, int w_support, int w_oversample,
+                             dg_dtype dtype, int device);
+
+/* Release the plan and every device buffer it owns.  Synchronises the
+ * plan's device first.  NULL is ignored. */
+void degrid_plan_destroy(degrid_plan_t plan);
+
+/*
+ * Tuning knobs of the persistent degridding / gridding kernels (the paper
+ * tunes N_b, the visibilities per thread block, by hand; Section "Results").
+ *   chunk            visibilities per work item claimed by one warp
+ *                    (multiple of 32, 32 .. 65536); a work item never
+ *                    straddles two subgrids
+ *   warps_per_block  warps per CTA (1 .. 32)
+ *   blocks_per_sm    resident CTAs per SM for the persistent grid
+ *                    (0 = as many as the occupancy calculator allows)
+ * Any argument <= 0 keeps the current value, except blocks_per_sm where 0
+ * selects the occupancy maximum and < 0 keeps the current value.
+ * Returns DG_OK or DG_ERR_ARG.
+ */
+dg_status degrid_plan_set_tuning(degrid_plan_t plan, int chunk, int warps_per_block,
+                                 int blocks_per_sm);
+
+/* Read back the current tuning (any pointer may be NULL). */
+dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_block,
+                                 int *blocks_per_sm);
+
+/*
+ * Kernel timing (profiling aid, not in the paper).  degrid_plan_enable_timing
+ * with n_slots > 0 creates n_slots CUDA event pairs; from then on every
+ * degrid_execute / grid_adjoint_execute records one pair on its stream around
+ * its main (persistent) kernel only, excluding the two small scheduling
+ * kernels, cycling through the slots.  n_slots = 0 disables timing and frees
+ * the events.  Disable timing before capturing calls into a CUDA graph.
+ *
+ * degrid_plan_kernel_times_ms synchronises on the newest pair and writes the
+ * durations (milliseconds) of the most recent min(capacity, launches,
+ * n_slots) timed launches to ms_out, oldest first, and their number to
+ * *count.  Timing another launch resets nothing: slots are reused in turn.
+ * Both return DG_OK, DG_ERR_ARG or DG_ERR_CUDA.
+ */
+dg_status degrid_plan_enable_timing(degrid_plan_t plan, int n_slots);
+dg_status degrid_plan_kernel_times_ms(degrid_plan_t plan, float *ms_out, int capacity,
+                                      int *count);
+
+/*
+ * Degridding (Section "Implementation", the weighted footprint sum):
+ *   vis_out[i] = sum_{b<8} sum_{a<8} sum_{c<4} g_uv[fv][b] g_uv[fu][a]
+ *                g_w[fw][c] * sub[s][y0+b][x0+a][z0+c]
+ * for every visibility i of subgrid s, in the order of uvw.
+ *   stream         cudaStream_t (as void*), NULL = legacy default stream
+ *   n_subgrids     S >= 0
+ *   subgrids       DEVICE, S * ny * nx * nz complex values in the plan's
+ *                  storage type (8 bytes each for DG_C64, 4 bytes otherwise);
+ *                  16-byte aligned
+ *   subgrid_scale  DEVICE float [S]; required for DG_C32_F16 / DG_C32_BF16,
+ *                  ignored (may be NULL) for DG_C64
+ *   uvw            DEVICE double [n_vis][3], 8-byte aligned
+ *   vis_offsets    DEVICE int64 [S + 1]
+ *   n_vis          N >= 0 (must equal vis_offsets[S])
+ *   vis_out        DEVICE float [n_vis][2] (complex64), 8-byte aligned;
+ *                  every element is written
+ * Accumulation is FP32; the coordinate step is exact integer arithmetic on
+ * the FP64 coordinates.  Malformed vis_offsets are flagged for
+ * degrid_get_status; subgrids with a negative count are skipped.
+ * The plan's scratch grows on the first call with a larger S or N; call once
+ * with the largest sizes before capturing the call in a CUDA graph.
+ */
+dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
+                         const void *subgrids, const float *subgrid_scale,
+                         const double *uvw, const int64_t *vis_offsets, int64_t n_vis,
+                         float *vis_out);
+
+/*
+ * Adjoint of degrid_execute (gridding): for every visibility i of subgrid s
+ *   sub_out[s][y0+b][x0+a][z0+c] += g_uv[fv][b] g_uv[fu][a] g_w[fw][c] * vis_in[i]
+ * (real weights, so the adjoint needs no conjugation).  sub_out is complex64
+ * [S][ny][nx][nz] on the DEVICE, zeroed first unless accumulate != 0.
+ * FP32 atomic accumulation: the summation order, and so the last bits, are
+ * not deterministic.  Other arguments as for degrid_execute.
+ */
+dg_status grid_adjoint_execute(degrid_plan_t plan, void *stream, int n_subgrids,
+                               const double *uvw, const int64_t *vis_offsets,
+                               int64_t n_vis, const float *vis_in, float *sub_out,
+                               int accumulate);
+
+/*
+ * Coordinate step alone (Section "Implementation": the start point g and the
+ * GCF locations of every visibility), as computed inside degrid_execute:
+ * coords_out DEVICE int32 [n_vis][6] = (x0, y0, z0, fu, fv, fw), all six -1
+ * for an invalid visibility (which is also counted for degrid_get_status).
+ */
+dg_status degrid_coords_execute(degrid_plan_t plan, void *stream, const double *uvw,
+                                int64_t n_vis, int32_t *coords_out);
+
+/*
+ * Convert complex64 subgrids to the reduced-precision storage used by
+ * DG_C32_F16 / DG_C32_BF16: scale[s] = max over subgrid s of
+ * max(|re|, |im|); code = round-to-nearest-even(component / scale) in the
+ * target format (FP32 division); an all-zero subgrid gets scale 0 and zero
+ * codes.  Not part of the paper (its subgrids are given); provided so that
+ * callers can produce the storage the kernels read.
+ *   dtype        DG_C32_F16 or DG_C32_BF16
+ *   elems        complex elements per subgrid (ny * nx * nz)
+ *   in           DEVICE float [S][elems][2]
+ *   codes_out    DEVICE uint16 [S][elems][2]
+ *   scale_out    DEVICE float [S]
+ */
+dg_status degrid_pack_subgrids(void *stream, dg_dtype dtype, int n_subgrids, int64_t elems,
+                               const float *in, void *codes_out, float *scale_out);
+
+/*
+ * Read and clear the device-side status of the plan: synchronises `stream`,
+ * stores the number of invalid visibilities seen since the last call in
+ * *n_invalid (may be NULL) and returns DG_ERR_OFFSETS if a call saw
+ * malformed vis_offsets, else DG_OK (or DG_ERR_CUDA).
+ */
+dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEGRID_H */

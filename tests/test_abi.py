@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every declared symbol (CPU only).
+
+No compute call is made: only the host-side argument checks, which return
+before any CUDA call, are exercised.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2102_12739_gb300 import _native, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "degrid.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load()
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    for want in ("degrid_plan_create", "degrid_plan_destroy", "degrid_execute",
+                 "grid_adjoint_execute", "degrid_get_status", "degrid_plan_set_tuning",
+                 "degrid_status_string", "degrid_coords_execute", "degrid_pack_subgrids"):
+        assert want in names
+    # the Python binding binds exactly what the header declares
+    assert set(names) == set(_native.SIGNATURES)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(build.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(raw, name), f"{name} not exported by libdegrid.so"
+
+
+def test_status_strings(lib):
+    assert lib.degrid_status_string(0) == b"ok"
+    assert b"offsets" in lib.degrid_status_string(_native.DG_ERR_OFFSETS)
+    assert b"sm_103a" in lib.degrid_version()
+
+
+def test_host_argument_checks_need_no_gpu(lib):
+    P = ctypes.c_void_p
+    g_uv = np.zeros((16384, 8))
+    g_w = np.zeros((128, 4))
+    h = P()
+    a, b = g_uv.ctypes.data_as(P), g_w.ctypes.data_as(P)
+    assert lib.degrid_plan_create(None, 512, 512, 4, a, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, None, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, a, 6, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_UNSUPPORTED
+    assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, a, 8, 10000, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 2, a, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_UNSUPPORTED
+    assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, a, 8, 16384, b, 4, 128, 7, 0) == _native.DG_ERR_DTYPE
+    assert h.value is None
+    assert lib.degrid_execute(None, None, 1, None, None, None, None, 0, None) == _native.DG_ERR_ARG
+    assert lib.grid_adjoint_execute(None, None, 1, None, None, 0, None, None, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_coords_execute(None, None, None, 0, None) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_set_tuning(None, 256, 8, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_get_status(None, None, None) == _native.DG_ERR_ARG
+    assert lib.degrid_pack_subgrids(None, 0, 1, 4, None, None, None) == _native.DG_ERR_DTYPE
+    assert lib.degrid_pack_subgrids(None, 1, -1, 4, None, None, None) == _native.DG_ERR_ARG

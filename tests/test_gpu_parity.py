@@ -1,0 +1,368 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Bar (from the method's statement of the target):
+  * indices and GCF rows bit-exact;
+  * complex64 subgrids: relative L2 error <= 2e-6 over all visibilities;
+  * FP16 / BF16 subgrids: <= 1e-3 / <= 8e-3 against the oracle on the
+    original complex64 subgrids (quantisation included).
+Small cases are compared element by element; the full-size workloads run in
+the launch configuration the benchmark times and are checked on sampled
+visibilities the oracle recomputes one by one.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_2102_12739_gb300 as dg  # noqa: E402
+from paper_2102_12739_gb300 import synth  # noqa: E402
+from tests.test_oracle import load_coord_cases  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+G_UV, G_W = synth.default_tables()
+SHAPE = synth.SUBGRID_SHAPE
+TOL = {"c64": 2e-6, "f16": 1e-3, "bf16": 8e-3}
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def plan():
+    p = dg.DegridPlan(device=dev())
+    yield p
+    p.close()
+
+
+def rel_l2(got, ref):
+    ref = np.asarray(ref)
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(np.asarray(got) - ref) / (den if den > 0 else 1.0)
+
+
+def upload(w: synth.Workload, sub=None):
+    d = dev()
+    sub = w.subgrids() if sub is None else sub
+    return (torch.from_numpy(np.ascontiguousarray(sub)).to(d),
+            torch.from_numpy(w.uvw).to(d), torch.from_numpy(w.vis_offsets).to(d))
+
+
+def small_workload(counts, kind="line", shape=SHAPE, seed=0):
+    """Lines ("line"), scattered points ("scatter") or segments/arcs ("mixed")."""
+    parts = []
+    for s, c in enumerate(counts):
+        rng = np.random.default_rng([100 + seed, s])
+        if kind == "line":
+            parts.append(synth.random_line(c, rng, shape))
+        elif kind == "mixed":
+            parts.append(synth.piecewise_list(c, rng, shape))
+        else:
+            ny, nx, _ = shape
+            u = rng.uniform(*synth.uv_box(nx), c)
+            v = rng.uniform(*synth.uv_box(ny), c)
+            w = rng.uniform(synth.W_LO, synth.W_HI, c)
+            parts.append(np.stack([u, v, w], axis=1))
+    uvw = np.ascontiguousarray(np.concatenate(parts)) if parts else np.zeros((0, 3))
+    return synth.Workload("small", len(counts), tuple(shape), uvw, synth.offsets_from_counts(counts))
+
+
+def oracle_degrid_sample(w: synth.Workload, subgrids_of, idx):
+    """Oracle values of visibilities `idx` (sorted global indices)."""
+    idx = np.sort(np.asarray(idx))
+    s_of = np.searchsorted(w.vis_offsets, idx, side="right") - 1
+    subs = np.unique(s_of)
+    sub = np.stack([subgrids_of(s).astype(np.complex128) for s in subs])
+    counts = [(s_of == s).sum() for s in subs]
+    ref, bad = oracle.degrid(G_UV, G_W, sub, w.uvw[idx], synth.offsets_from_counts(counts))
+    return idx, ref
+
+
+# ---------------------------------------------------------------------------
+# coordinates: bit-exact
+# ---------------------------------------------------------------------------
+
+def test_coords_hand_cases(plan):
+    uvw, expect = load_coord_cases()
+    got = plan.coords(torch.from_numpy(uvw).to(dev())).cpu().numpy()
+    np.testing.assert_array_equal(got, expect)
+    assert plan.status() == int((expect[:, 0] < 0).sum())
+
+
+def test_coords_random_and_ties_bit_exact(plan):
+    rng = np.random.default_rng(5)
+    n = 400_000
+    u = rng.uniform(-20, 540, n)
+    # exact ties k + 1/2 at the oversampled resolution, and their neighbours
+    k = rng.integers(0, 512 * 16384, n // 4)
+    u[: n // 4] = (k + 0.5) / 16384.0
+    u[n // 4: n // 2] = np.nextafter((k + 0.5) / 16384.0, np.inf)
+    v = rng.uniform(-20, 540, n)
+    v[: n // 4] = (rng.integers(0, 512 * 16384, n // 4) + 0.5) / 16384.0
+    w = rng.uniform(0.9, 2.1, n)
+    w[: n // 4] = (rng.integers(100, 270, n // 4) + 0.5) / 128.0
+    special = [np.nan, np.inf, -np.inf, 0.0, -0.0, 5e-324, 1e300, -1e300, 2.0 ** 48, 2.0 ** 49]
+    u[-len(special):] = special
+    uvw = np.stack([u, v, w], axis=1)
+    want, bad = oracle.coords(uvw, SHAPE)
+    got = plan.coords(torch.from_numpy(uvw).to(dev())).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert plan.status() == bad
+
+
+def test_coords_of_full_lines_workload(plan):
+    w = synth.workload("lines64_250k")
+    got = plan.coords(torch.from_numpy(w.uvw).to(dev())).cpu().numpy()
+    want, bad = oracle.coords(w.uvw, SHAPE)
+    assert bad == 0
+    np.testing.assert_array_equal(got, want)
+    assert plan.status() == 0
+
+
+# ---------------------------------------------------------------------------
+# degridding values
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["line", "scatter", "mixed"])
+def test_degrid_small_elementwise(plan, kind):
+    # several chunks, a ragged tail, an empty subgrid, invalid visibilities
+    w = small_workload([1000, 0, 777, 33], kind=kind)
+    w.uvw[5] = [np.nan, 10.0, 1.5]
+    w.uvw[1200] = [600.0, 10.0, 1.5]
+    w.uvw[1776] = [20.0, 20.0, 0.2]
+    sub_np = synth.subgrid_stack(4)
+    sub, uvw, offs = upload(w, sub_np)
+    got = plan.degrid(sub, uvw, offs).cpu().numpy()
+    n_bad = plan.status()
+    ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert n_bad == bad == 3
+    assert got[5] == 0 and got[1200] == 0 and got[1776] == 0
+    assert rel_l2(got, ref) <= TOL["c64"]
+
+
+def test_degrid_line1_20k_full(plan):
+    w = synth.workload("line1_20k")
+    sub_np = synth.subgrid_stack(1)
+    sub, uvw, offs = upload(w, sub_np)
+    got = plan.degrid(sub, uvw, offs).cpu().numpy()
+    ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert bad == 0 and plan.status() == 0
+    assert rel_l2(got, ref) <= TOL["c64"]
+    # every visibility individually close, relative to the footprint scale
+    assert np.max(np.abs(got - ref)) <= 1e-5
+
+
+def test_degrid_lines64_full_size_sampled(plan):
+    # the throughput workload, in the benchmark's default launch configuration
+    w = synth.workload("lines64_250k")
+    sub, uvw, offs = upload(w)
+    got = plan.degrid(sub, uvw, offs).cpu().numpy()
+    assert plan.status() == 0
+    rng = np.random.default_rng(7)
+    picks = []
+    for s in (0, 1, 31, 63):
+        lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
+        picks += [lo, hi - 1] + list(rng.integers(lo, hi, 1500))
+    idx, ref = oracle_degrid_sample(w, w.subgrid, np.unique(picks))
+    assert rel_l2(got[idx], ref) <= TOL["c64"]
+    assert np.all(np.isfinite(got))
+
+
+def test_degrid_batched512_sampled(plan):
+    w = synth.workload("batched512")
+    d = dev()
+    sub = torch.empty((w.n_subgrids,) + SHAPE, dtype=torch.complex64, device=d)
+    for s in range(w.n_subgrids):
+        sub[s].copy_(torch.from_numpy(w.subgrid(s)))
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    got = plan.degrid(sub, uvw, offs).cpu().numpy()
+    assert plan.status() == 0
+    rng = np.random.default_rng(8)
+    counts = w.counts()
+    chosen = [int(np.argmin(counts)), int(np.argmax(counts))] + list(rng.integers(0, 512, 4))
+    picks = []
+    for s in chosen:
+        lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
+        picks += [lo, hi - 1] + list(rng.integers(lo, hi, 800))
+    idx, ref = oracle_degrid_sample(w, w.subgrid, np.unique(picks))
+    assert rel_l2(got[idx], ref) <= TOL["c64"]
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_reduced_precision_storage(dtype):
+    d = dev()
+    w = small_workload([3000, 1, 2500], kind="mixed", seed=3)
+    sub_np = synth.subgrid_stack(3)
+    sub_np[1] *= 1e-3                       # subgrids with different scales
+    sub_c64 = torch.from_numpy(sub_np).to(d)
+    codes, scale = dg.pack_subgrids(sub_c64, dtype)
+    want_codes, want_scale = oracle.quantize(sub_np, dtype)
+    np.testing.assert_array_equal(scale.cpu().numpy(), want_scale)
+    got_codes = codes.view(torch.int16).cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(got_codes, want_codes)
+    with dg.DegridPlan(dtype=dtype, device=d) as p:
+        uvw = torch.from_numpy(w.uvw).to(d)
+        offs = torch.from_numpy(w.vis_offsets).to(d)
+        got = p.degrid(codes, uvw, offs, scale=scale).cpu().numpy()
+    ref, _ = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert rel_l2(got, ref) <= TOL[dtype]
+    # against the oracle on the stored (dequantised) values: kernel error only
+    deq = oracle.dequantize(want_codes, want_scale, dtype)
+    ref_q, _ = oracle.degrid(G_UV, G_W, deq, w.uvw, w.vis_offsets)
+    assert rel_l2(got, ref_q) <= 2e-6
+
+
+# ---------------------------------------------------------------------------
+# adjoint and autograd
+# ---------------------------------------------------------------------------
+
+def test_adjoint_matches_oracle(plan):
+    d = dev()
+    shape = (64, 48, 4)
+    w = small_workload([700, 0, 1500], kind="mixed", shape=shape, seed=9)
+    y = synth.adjoint_vis(w.n_vis)
+    with dg.DegridPlan(shape=shape, device=d) as p:
+        got = p.grid(torch.from_numpy(y).to(d), torch.from_numpy(w.uvw).to(d),
+                     torch.from_numpy(w.vis_offsets).to(d), w.n_subgrids).cpu().numpy()
+        ref, _ = oracle.grid(G_UV, G_W, shape, w.n_subgrids, w.uvw, w.vis_offsets, y)
+        assert rel_l2(got, ref) <= TOL["c64"]
+        # accumulate mode adds to what is there
+        base = torch.ones((w.n_subgrids,) + shape, dtype=torch.complex64, device=d)
+        acc = p.grid(torch.from_numpy(y).to(d), torch.from_numpy(w.uvw).to(d),
+                     torch.from_numpy(w.vis_offsets).to(d), w.n_subgrids, out=base,
+                     accumulate=True).cpu().numpy()
+        assert rel_l2(acc - 1, ref) <= TOL["c64"]
+
+
+def test_adjoint_dot_product_identity_on_gpu(plan):
+    d = dev()
+    w = synth.workload("line1_20k")
+    sub_np = synth.subgrid_stack(1)
+    sub, uvw, offs = upload(w, sub_np)
+    y = synth.adjoint_vis(w.n_vis)
+    ds = plan.degrid(sub, uvw, offs).cpu().numpy().astype(np.complex128)
+    gy = plan.grid(torch.from_numpy(y).to(d), uvw, offs, 1).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(ds, y.astype(np.complex128))
+    rhs = np.vdot(sub_np.astype(np.complex128), gy)
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_autograd_gradient_is_adjoint_of_residual(plan):
+    d = dev()
+    w = small_workload([4000, 2000], kind="line", seed=11)
+    sub_np = synth.subgrid_stack(2)
+    y = synth.adjoint_vis(w.n_vis)
+    sub = torch.from_numpy(sub_np).to(d).requires_grad_(True)
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    vis = dg.DegridFn.apply(sub, uvw, offs, plan)
+    loss = (vis - torch.from_numpy(y).to(d)).abs().pow(2).sum()
+    loss.backward()
+    got = sub.grad.cpu().numpy()
+    ref_vis, _ = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    ref, _ = oracle.grid(G_UV, G_W, SHAPE, 2, w.uvw, w.vis_offsets, 2 * (ref_vis - y))
+    assert rel_l2(got, ref) <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# scheduler, edge cases, graphs
+# ---------------------------------------------------------------------------
+
+def test_tunings_give_bitwise_identical_results(plan):
+    w = small_workload([5000, 255, 256, 257, 0, 1, 31, 33], kind="mixed", seed=12)
+    sub, uvw, offs = upload(w, synth.subgrid_stack(8))
+    outs = []
+    saved = plan.tuning()
+    try:
+        for chunk, warps, bps in [(32, 1, 1), (256, 8, 0), (4096, 4, 2), (96, 2, 0)]:
+            plan.set_tuning(chunk, warps, bps)
+            outs.append(plan.degrid(sub, uvw, offs).cpu().numpy())
+    finally:
+        plan.set_tuning(saved["chunk"], saved["warps_per_block"], saved["blocks_per_sm"])
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o.view(np.uint64), outs[0].view(np.uint64))
+
+
+def test_one_subgrid_at_a_time_matches_batched(plan):
+    w = small_workload([900, 2100, 64], kind="mixed", seed=13)
+    sub_np = synth.subgrid_stack(3)
+    sub, uvw, offs = upload(w, sub_np)
+    batched = plan.degrid(sub, uvw, offs).cpu().numpy()
+    d = dev()
+    for s in range(3):
+        lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
+        one = plan.degrid(sub[s:s + 1].contiguous(), uvw[lo:hi].contiguous(),
+                          torch.tensor([0, hi - lo], dtype=torch.int64, device=d)).cpu().numpy()
+        np.testing.assert_array_equal(one.view(np.uint64), batched[lo:hi].view(np.uint64))
+
+
+def test_empty_and_degenerate_inputs(plan):
+    d = dev()
+    sub = torch.zeros((2,) + SHAPE, dtype=torch.complex64, device=d)
+    uvw = torch.zeros((0, 3), dtype=torch.float64, device=d)
+    offs = torch.zeros(3, dtype=torch.int64, device=d)
+    assert plan.degrid(sub, uvw, offs).numel() == 0
+    g = plan.grid(torch.zeros(0, dtype=torch.complex64, device=d), uvw, offs, 2)
+    assert torch.count_nonzero(g).item() == 0
+    # a single visibility
+    w = small_workload([1], seed=14)
+    sub_np = synth.subgrid_stack(1)
+    s1, u1, o1 = upload(w, sub_np)
+    got = plan.degrid(s1, u1, o1).cpu().numpy()
+    ref, _ = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert rel_l2(got, ref) <= TOL["c64"]
+    assert plan.status() == 0
+
+
+def test_malformed_offsets_are_reported(plan):
+    d = dev()
+    w = small_workload([100, 100], seed=15)
+    sub, uvw, _ = upload(w, synth.subgrid_stack(2))
+    bad = torch.tensor([0, 150, 120], dtype=torch.int64, device=d)   # ends short of N, decreasing
+    plan.degrid(sub, uvw, torch.tensor([0, 150, 200], dtype=torch.int64, device=d))
+    assert plan.status() == 0
+    plan.degrid(sub, uvw, bad)
+    with pytest.raises(dg.DegridError) as e:
+        plan.status()
+    assert e.value.status == dg.DG_ERR_OFFSETS
+    assert plan.status() == 0      # cleared
+
+
+def test_argument_errors_raise(plan):
+    d = dev()
+    sub = torch.zeros((1,) + SHAPE, dtype=torch.complex64, device=d)
+    uvw = torch.zeros((4, 3), dtype=torch.float64, device=d)
+    with pytest.raises((TypeError, ValueError)):
+        plan.degrid(sub, uvw.float(), torch.tensor([0, 4], device=d))
+    with pytest.raises((TypeError, ValueError)):
+        plan.degrid(sub, uvw, torch.tensor([0, 4], dtype=torch.int64, device=d)[None])
+    with dg.DegridPlan(dtype="bf16", device=d) as p:
+        with pytest.raises(ValueError):
+            p.degrid(torch.zeros((1,) + SHAPE + (2,), dtype=torch.bfloat16, device=d), uvw,
+                     torch.tensor([0, 4], dtype=torch.int64, device=d))
+
+
+def test_cuda_graph_replay_is_identical(plan):
+    d = dev()
+    w = small_workload([3000, 500, 4500], kind="mixed", seed=16)
+    sub, uvw, offs = upload(w, synth.subgrid_stack(3))
+    ref = plan.degrid(sub, uvw, offs)           # sizes the scratch before capture
+    out = torch.empty_like(ref)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=d)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.degrid(sub, uvw, offs, out=out)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out.view(torch.float32), ref.view(torch.float32))
