@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named workload (paper_2102_12739_gb300.synth.workload); the "
+                         "default is the throughput configuration, others serve profiling")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--sweep-steps", type=int, default=500)
     ap.add_argument("--no-e2e", action="store_true")
@@ -235,7 +238,7 @@ def run_ours(args, rank, world):
     peaks, peaks_src = measured_peaks()
 
     g_uv, g_w = synth.default_tables()
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     sub_np = w.subgrids()
     sub = torch.from_numpy(sub_np).to(dev)
     uvw = torch.from_numpy(w.uvw).to(dev)
@@ -302,7 +305,8 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC, "n_vis": w.n_vis,
+        "config": {"workload": (WORKLOAD + ": " + WORKLOAD_DESC) if args.workload == WORKLOAD
+                   else args.workload, "n_vis": w.n_vis,
                    "subgrid_storage": "complex64",
                    "l2": "flushed before every step (256 MB write outside the step events)",
                    "parallelism": "independent subgrid shards, one per GPU" if world > 1 else "1 GPU",

@@ -274,6 +274,7 @@ def workload(name: str) -> Workload:
     line1_20k      1 subgrid, 20,000 visibilities on one line
     lines64_250k   64 subgrids, 250,000 visibilities each (16M): the
                    throughput workload
+    lines16_250k   its first 16 subgrids (4M visibilities; profiling case)
     batched512     512 subgrids, log-uniform counts in [1e3, 1e6]
     diff32_100k    32 subgrids, 100,000 visibilities each (adjoint)
     """
@@ -281,6 +282,8 @@ def workload(name: str) -> Workload:
         return lines_workload(name, [20_000])
     if name == "lines64_250k":
         return lines_workload(name, [250_000] * 64)
+    if name == "lines16_250k":
+        return lines_workload(name, [250_000] * 16)
     if name == "batched512":
         return batched_workload(name, 512)
     if name == "diff32_100k":
