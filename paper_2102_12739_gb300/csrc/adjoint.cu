@@ -51,7 +51,6 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw,
     const int a = lane >> 2, c = lane & 3;
     const int lane_off = a * g.nz + c;
     const int total = *sched.n_chunks;
-    const int64_t *offs = sched.vis_offsets;
 
     for (;;) {
         int k = 0;
@@ -60,10 +59,10 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw,
         k = __shfl_sync(kFull, k, 0);
         if (k >= total)
             break;
-        const ChunkRef ref = sched.chunks[k];
-        const int64_t lo = offs[ref.s] + (int64_t)ref.j * sched.chunk;
-        const int64_t hi = min(lo + (int64_t)sched.chunk, offs[ref.s + 1]);
-        float2 *const sub = sub_out + (int64_t)ref.s * g.plane + lane_off;
+        const ChunkDesc cd = sched.chunks[k];
+        const int64_t lo = cd.lo;
+        const int64_t hi = lo + cd.n;
+        float2 *const sub = sub_out + (int64_t)cd.s * g.plane + lane_off;
 
         int cur = -1;           // footprint key accumulated in A (-1: none)
         float2 A[kUV];
@@ -135,7 +134,8 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
                               float *sub_out, int grid_blocks)
 {
     using namespace dg;
-    Schedule sched{vis_offsets, p->chunks, p->n_chunks, p->work_counter, p->chunk};
+    (void)vis_offsets;
+    Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = sizeof(WarpTile) * p->warps_per_block;
     adjoint_kernel<<<grid_blocks, threads, smem, st>>>(

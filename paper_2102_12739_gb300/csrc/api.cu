@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "internal.cuh"
 
 cudaError_t dg_launch_pack(cudaStream_t st, dg_dtype dtype, int n_subgrids, int64_t elems,
@@ -80,11 +82,37 @@ void free_plan_buffers(degrid_plan *p)
     free_events(p);
     cudaFree(p->guv);
     cudaFree(p->gw);
+    cudaFree(p->guv2);
+    cudaFree(p->gw2);
     cudaFree(p->status);
     cudaFree(p->work_counter);
     cudaFree(p->n_chunks);
     cudaFree(p->prefix);
     cudaFree(p->chunks);
+}
+
+// TMA descriptor of a row-major FP32 table [rows][cols]; one box = one row,
+// as tile::gather4 requires.
+dg_status encode_row_table(CUtensorMap *tm, float *table, int rows, int cols)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return DG_ERR_CUDA;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)cols, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, table, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DG_OK : DG_ERR_CUDA;
 }
 
 // Grows the schedule scratch so that S subgrids and n_vis visibilities fit.
@@ -216,11 +244,13 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     p->geo.log2_w_os = l2w;
     p->geo.row_stride = nx * nz;
     p->geo.plane = (int64_t)nx * ny * nz;
+    // small w tables (32 bytes per duplicated row) live in each CTA's shared memory
+    p->geo.w_table_rows = (size_t)w_oversample * 2 * w_support * sizeof(float) <= 16 * 1024 ? w_oversample : 0;
     p->uv_oversample = uv_oversample;
     p->w_oversample = w_oversample;
     p->dtype = dtype;
     p->chunk = 256;
-    p->warps_per_block = 8;
+    p->warps_per_block = dg_max_warps_per_block();
     p->blocks_per_sm = 0;
 
     dg_status st = DG_OK;
@@ -229,8 +259,17 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
         h_uv[i] = (float)g_uv[i];            // round to nearest
     for (size_t i = 0; i < h_w.size(); ++i)
         h_w[i] = (float)g_w[i];
+    // the same values with every tap stored twice: (g, g) pairs are ready
+    // operands of the packed FP32 FMAs of the degridding kernel
+    std::vector<float> h_uv2(2 * h_uv.size()), h_w2(2 * h_w.size());
+    for (size_t i = 0; i < h_uv.size(); ++i)
+        h_uv2[2 * i] = h_uv2[2 * i + 1] = h_uv[i];
+    for (size_t i = 0; i < h_w.size(); ++i)
+        h_w2[2 * i] = h_w2[2 * i + 1] = h_w[i];
     if ((st = dev_alloc(&p->guv, h_uv.size())) != DG_OK ||
         (st = dev_alloc(&p->gw, h_w.size())) != DG_OK ||
+        (st = dev_alloc(&p->guv2, h_uv2.size())) != DG_OK ||
+        (st = dev_alloc(&p->gw2, h_w2.size())) != DG_OK ||
         (st = dev_alloc(&p->status, 1)) != DG_OK ||
         (st = dev_alloc(&p->work_counter, 1)) != DG_OK ||
         (st = dev_alloc(&p->n_chunks, 1)) != DG_OK) {
@@ -242,6 +281,10 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     if (e == cudaSuccess)
         e = cudaMemcpy(p->gw, h_w.data(), sizeof(float) * h_w.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
+        e = cudaMemcpy(p->guv2, h_uv2.data(), sizeof(float) * h_uv2.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->gw2, h_w2.data(), sizeof(float) * h_w2.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
         e = cudaMemset(p->status, 0, sizeof(dg::DeviceStatus));
     if (e == cudaSuccess)
         e = cudaMemset(p->work_counter, 0, sizeof(int));
@@ -251,6 +294,12 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
         free_plan_buffers(p);
         delete p;
         return from_cuda(e);
+    }
+    if ((st = encode_row_table(&p->tm_uv2, p->guv2, uv_oversample, 2 * uv_support)) != DG_OK ||
+        (st = encode_row_table(&p->tm_w2, p->gw2, w_oversample, 2 * w_support)) != DG_OK) {
+        free_plan_buffers(p);
+        delete p;
+        return st;
     }
     *out = p;
     return DG_OK;
@@ -272,7 +321,7 @@ dg_status degrid_plan_set_tuning(degrid_plan_t p, int chunk, int warps_per_block
         return DG_ERR_ARG;
     if (chunk > 0 && (chunk % dg::kWarp != 0 || chunk > 65536))
         return DG_ERR_ARG;
-    if (warps_per_block > 8)
+    if (warps_per_block > dg_max_warps_per_block())
         return DG_ERR_ARG;
     if (blocks_per_sm > 64)
         return DG_ERR_ARG;

@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -25,56 +26,38 @@ struct Geometry {
     int log2_w_os;      // w oversampling = 2^log2_w_os
     int row_stride;     // elements between rows y and y + 1: nx * nz
     int64_t plane;      // elements per subgrid: ny * nx * nz
+    int w_table_rows;   // w oversampling if the w table is staged in shared memory, else 0
 };
 
 // ---------------------------------------------------------------------------
 // Coordinate step (Section "Implementation": start point g and GCF rows).
 //
-// p = rint(q * 2^k) with ties to even is computed exactly with integer
-// operations on the IEEE-754 bit pattern of q, so no FP64 arithmetic is
-// issued (FP64 throughput is low on this part).  With m the 53-bit
-// significand and e the biased exponent, |q| * 2^k = m * 2^(e - 1075 + k).
-// Returns false for non-finite q or |q * 2^k| >= 2^62.
+// Per axis with support W and oversampling O = 2^k: p = rint(q * O) with
+// ties to even, i = floor(p / O), f = p - i * O, start = i - W/2 + 1; valid
+// when 0 <= start <= n - W.  Computed exactly with integer operations on the
+// IEEE-754 pattern of q, without FP64 arithmetic (FP64 runs at 1/64 of the
+// FP32 rate on this part):
+//   * q <= 0 (including -0, negative NaN) gives p <= 0, i <= 0, start < 0;
+//   * with m the 53-bit significand and e the biased exponent,
+//     q * O = m * 2^-r, r = 1075 - k - e.  r > 53 means q * O < 0.5, so
+//     p = 0 and start < 0; r < 1 means q * O >= 2^52 (or q is inf / NaN),
+//     far beyond any subgrid (n * O < 2^52).  All these are invalid;
+//   * otherwise p = (m + 2^(r-1) - 1 + bit_r(m)) >> r, which is m / 2^r
+//     rounded to nearest with ties to the even neighbour.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool snap_rint(double q, int log2_os, long long &p)
-{
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(q);
-    const int e = (int)((bits >> 52) & 0x7ff);
-    if (e == 0x7ff)
-        return false;                       // inf / nan
-    const unsigned long long m = (bits & 0x000fffffffffffffull) | (e ? 0x0010000000000000ull : 0ull);
-    const int shift = (e ? e : 1) - 1075 + log2_os;
-    unsigned long long mag;
-    if (shift >= 0) {
-        if (shift > 9)
-            return false;                   // |q * O| >= 2^62
-        mag = m << shift;
-    } else {
-        const int r = -shift;
-        if (r > 54) {
-            mag = 0;                        // |q * O| < 0.25
-        } else {
-            const unsigned long long whole = m >> r;
-            const unsigned long long rem = m & ((1ull << r) - 1ull);
-            const unsigned long long half = 1ull << (r - 1);
-            mag = whole + ((rem > half || (rem == half && (whole & 1ull))) ? 1ull : 0ull);
-        }
-    }
-    p = (bits >> 63) ? -(long long)mag : (long long)mag;
-    return true;
-}
-
-// One axis: start = floor(p / O) - W/2 + 1 and f = p mod O; valid when the
-// footprint lies in [0, n).
 __device__ __forceinline__ bool snap_axis(double q, int log2_os, int support, int n,
                                           int &start, int &frac)
 {
-    long long p;
-    if (!snap_rint(q, log2_os, p))
+    const long long bits = __double_as_longlong(q);
+    if (bits <= 0)
         return false;
-    const long long i = p >> log2_os;       // arithmetic shift = floor division
-    frac = (int)(p & ((1ll << log2_os) - 1));
-    const long long s = i - support / 2 + 1;
+    const int r = 1075 - log2_os - (int)(bits >> 52);
+    if (r < 1 || r > 53)
+        return false;
+    const unsigned long long m = ((unsigned long long)bits & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const unsigned long long p = (m + ((1ull << (r - 1)) - 1ull) + ((m >> r) & 1ull)) >> r;
+    frac = (int)(p & ((1ull << log2_os) - 1ull));
+    const long long s = (long long)(p >> log2_os) - support / 2 + 1;
     start = (int)s;
     return s >= 0 && s <= (long long)(n - support);
 }
@@ -131,27 +114,31 @@ struct DeviceStatus {
 };
 constexpr unsigned long long kFlagOffsets = 1ull;
 constexpr unsigned long long kFlagCapacity = 2ull;
+constexpr unsigned long long kFlagTimeout = 4ull;   // a bounded device wait gave up
 
-// Work decomposition: chunk k covers visibilities
-// [vis_offsets[s] + j * chunk, min(... + chunk, vis_offsets[s + 1])).
-struct ChunkRef {
+// Work decomposition: chunk k covers the n visibilities [lo, lo + n) of
+// subgrid s (n <= chunk size; a chunk never straddles two subgrids).
+struct alignas(16) ChunkDesc {
     int s;
-    int j;
+    int n;
+    long long lo;
 };
 
 struct Schedule {
-    const int64_t *vis_offsets;
-    const ChunkRef *chunks;
+    const ChunkDesc *chunks;
     const int *n_chunks;            // device scalar written by the scheduler
-    int *work_counter;              // zeroed before every launch
-    int chunk;
+    int *work_counter;              // zeroed by the scheduler before every launch
 };
 
 // Launch helpers implemented in schedule.cu.
 cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_subgrids,
                             int64_t n_vis, int chunk, int *prefix, int *n_chunks,
-                            ChunkRef *chunks, int capacity, int *work_counter,
+                            ChunkDesc *chunks, int capacity, int *work_counter,
                             DeviceStatus *status);
+
+// Bound on the polls of any device-side wait (mbarrier phase); a wait that
+// exceeds it records kFlagTimeout and the warp stops working.
+constexpr int kSpinLimit = 1 << 22;
 
 }  // namespace dg
 
@@ -164,11 +151,15 @@ struct degrid_plan {
     dg_dtype dtype;
     float *guv;                 // device FP32 [uv_os][8]
     float *gw;                  // device FP32 [w_os][4]
+    float *guv2;                // device FP32 [uv_os][8][2]: every tap twice
+    float *gw2;                 // device FP32 [w_os][4][2]
+    CUtensorMap tm_uv2;         // TMA descriptors of guv2 / gw2 (rows of 64 / 32 B)
+    CUtensorMap tm_w2;
     dg::DeviceStatus *status;   // device
     int *work_counter;          // device [1]
     int *n_chunks;              // device [1]
     int *prefix;                // device [cap_subgrids + 1]
-    dg::ChunkRef *chunks;       // device [cap_chunks]
+    dg::ChunkDesc *chunks;      // device [cap_chunks]
     int cap_subgrids;
     int cap_chunks;
     int chunk;
@@ -191,4 +182,5 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
 cudaError_t dg_launch_coords(degrid_plan *p, cudaStream_t st, const double *uvw,
                              int64_t n_vis, int32_t *coords_out);
 int dg_max_blocks_per_sm_degrid(degrid_plan *p);
+int dg_max_warps_per_block();   // largest CTA the kernels are compiled for
 int dg_max_blocks_per_sm_adjoint(degrid_plan *p);

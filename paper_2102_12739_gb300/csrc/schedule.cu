@@ -12,7 +12,7 @@
 // graph:
 //   1. chunk_prefix: one block validates vis_offsets and scans
 //      ceil(count_s / chunk) into prefix[S + 1];
-//   2. chunk_fill: writes (s, j) for every chunk.
+//   2. chunk_fill: writes (s, count, first visibility) for every chunk.
 #include "internal.cuh"
 
 namespace dg {
@@ -87,12 +87,17 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
     }
 }
 
-__global__ void chunk_fill(const int *__restrict__ prefix, int S, ChunkRef *__restrict__ chunks)
+__global__ void chunk_fill(const int *__restrict__ prefix, const int64_t *__restrict__ offs,
+                           int S, int chunk, ChunkDesc *__restrict__ chunks)
 {
     for (int s = blockIdx.x; s < S; s += gridDim.x) {
         const int lo = prefix[s], hi = prefix[s + 1];
-        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x)
-            chunks[k] = ChunkRef{s, k - lo};
+        const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
+        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+            const int64_t first = vis_lo + (int64_t)(k - lo) * chunk;
+            const int64_t last = min(first + (int64_t)chunk, vis_hi);
+            chunks[k] = ChunkDesc{s, (int)(last - first), (long long)first};
+        }
     }
 }
 
@@ -100,7 +105,7 @@ __global__ void chunk_fill(const int *__restrict__ prefix, int S, ChunkRef *__re
 
 cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_subgrids,
                             int64_t n_vis, int chunk, int *prefix, int *n_chunks,
-                            ChunkRef *chunks, int capacity, int *work_counter,
+                            ChunkDesc *chunks, int capacity, int *work_counter,
                             DeviceStatus *status)
 {
     chunk_prefix<<<1, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, prefix,
@@ -109,7 +114,7 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
     if (err != cudaSuccess || n_subgrids == 0)
         return err;
     const int blocks = n_subgrids < 4096 ? n_subgrids : 4096;
-    chunk_fill<<<blocks, 256, 0, st>>>(prefix, n_subgrids, chunks);
+    chunk_fill<<<blocks, 256, 0, st>>>(prefix, vis_offsets, n_subgrids, chunk, chunks);
     return cudaGetLastError();
 }
 
