@@ -58,7 +58,8 @@ typedef enum {
     DG_ERR_OOM = 3,            /* a device allocation failed */
     DG_ERR_DTYPE = 4,          /* storage type not supported / scale missing */
     DG_ERR_OFFSETS = 5,        /* vis_offsets malformed (found on the device) */
-    DG_ERR_UNSUPPORTED = 6     /* GCF support / subgrid shape not supported */
+    DG_ERR_UNSUPPORTED = 6,    /* GCF support / subgrid shape not supported */
+    DG_ERR_SCRATCH_LIMIT = 7   /* sizes exceed the fixed scratch of degrid_execute_noalloc */
 } dg_status;
 
 /* Subgrid storage: complex64, or FP16 / BF16 (re, im) pairs with one FP32
@@ -212,6 +213,50 @@ dg_status degrid_pack_subgrids(void *stream, dg_dtype dtype, int n_subgrids, int
  * malformed vis_offsets, else DG_OK (or DG_ERR_CUDA).
  */
 dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid);
+
+/*
+ * Degridding without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc once they
+ * are running, such as real-time pipelines that must not enter the CUDA
+ * allocator after start-up (allocation and release can synchronise the
+ * device and stall every other stream) and hosts whose device-memory budget
+ * is owned entirely by another allocator.
+ *
+ * It computes the same visibilities as degrid_execute, but takes no plan:
+ *   g_uv, g_w      DEVICE float tables [uv_oversample][8] and [w_oversample][4]
+ *                  (the FP32 values degrid_plan_create would store)
+ *   nx, ny, nz,    as for degrid_plan_create (supports 8 and 4 implied)
+ *   uv_oversample, w_oversample, dtype
+ *   status_out     DEVICE unsigned long long [2] or NULL: receives the number
+ *                  of invalid visibilities and error flags (bit 0: malformed
+ *                  vis_offsets) of this call; zeroed by the call
+ * and the remaining arguments as for degrid_execute.  Every call is
+ * asynchronous on `stream` and uses the device that is current.
+ *
+ * All scratch comes from one fixed array of DG_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  Calls with
+ * uv_oversample > DG_NOALLOC_MAX_UV_OVERSAMPLE, w_oversample >
+ * DG_NOALLOC_MAX_W_OVERSAMPLE, n_subgrids > DG_NOALLOC_MAX_SUBGRIDS or
+ * n_vis > DG_NOALLOC_MAX_VIS are rejected with DG_ERR_SCRATCH_LIMIT before
+ * anything is enqueued.  The array is shared by all calls on a device and
+ * keeps what the previous call left, so calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race with each other and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.
+ */
+#define DG_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+#define DG_NOALLOC_MAX_UV_OVERSAMPLE 16384
+#define DG_NOALLOC_MAX_W_OVERSAMPLE 512
+#define DG_NOALLOC_MAX_SUBGRIDS 1024
+#define DG_NOALLOC_MAX_VIS (1 << 25)
+dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz,
+                                 const float *g_uv, int uv_oversample,
+                                 const float *g_w, int w_oversample, dg_dtype dtype,
+                                 int n_subgrids, const void *subgrids,
+                                 const float *subgrid_scale, const double *uvw,
+                                 const int64_t *vis_offsets, int64_t n_vis,
+                                 float *vis_out, unsigned long long *status_out);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ DG_ERR_OOM = 3
 DG_ERR_DTYPE = 4
 DG_ERR_OFFSETS = 5
 DG_ERR_UNSUPPORTED = 6
+DG_ERR_SCRATCH_LIMIT = 7
 
 DG_C64 = 0
 DG_C32_F16 = 1
@@ -44,6 +45,8 @@ SIGNATURES = {
     "degrid_coords_execute": (_I, [_P, _P, _P, _I64, _P]),
     "degrid_pack_subgrids": (_I, [_P, _I, _I, _I64, _P, _P, _P]),
     "degrid_get_status": (_I, [_P, _P, ctypes.POINTER(_I64)]),
+    "degrid_execute_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
+                                    _I64, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -194,6 +194,7 @@ const char *degrid_status_string(dg_status status)
     case DG_ERR_DTYPE: return "unsupported storage type or missing scale";
     case DG_ERR_OFFSETS: return "malformed vis_offsets";
     case DG_ERR_UNSUPPORTED: return "unsupported GCF support or subgrid shape";
+    case DG_ERR_SCRATCH_LIMIT: return "sizes exceed the fixed scratch of degrid_execute_noalloc";
     }
     return "unknown status";
 }
