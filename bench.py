@@ -207,6 +207,20 @@ def sampled_error(plan_out, w, g_uv, g_w, subgrids_np, n_subgrids=4, per=2000, s
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), float(np.max(np.abs(got - ref)))
 
 
+def warm_up(torch, call, flush_buf, steps, min_seconds=1.0):
+    """At least `steps` (>= 3) untimed steps, and at least `min_seconds` of them,
+    so that clocks have ramped up before the timed region."""
+    t0 = time.perf_counter()
+    done = 0
+    while done < max(steps, 3) or time.perf_counter() - t0 < min_seconds:
+        flush_buf.zero_()
+        call()
+        done += 1
+        if done % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+
+
 def time_steps(torch, plan, call, steps, flush_buf, stream):
     """Run `steps` calls with an L2 flush before each; return per-step event
     times (ms) and per-launch main-kernel times (ms)."""
@@ -253,10 +267,7 @@ def run_ours(args, rank, world):
     def step():
         plan.degrid(sub, uvw, offs, out=out)
 
-    for _ in range(max(args.warmup, 3)):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    warm_up(torch, step, flush, args.warmup)
     assert plan.status() == 0
 
     sampler = ClockSampler(gpu_query_id(torch, dev)) if rank == 0 else None
@@ -329,8 +340,7 @@ def run_ours(args, rank, world):
 
                 def step2():
                     p2.degrid(codes, uvw, offs, scale=scale, out=o2)
-                for _ in range(max(args.warmup, 3)):
-                    step2()
+                warm_up(torch, step2, flush, args.warmup, min_seconds=0.3)
                 s_ms, k_ms = time_steps(torch, p2, step2, args.sweep_steps, flush, stream)
                 e = sampled_error(o2.cpu().numpy(), w, g_uv, g_w, sub_np)
             ms = sum(s_ms) / len(s_ms)

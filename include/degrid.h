@@ -245,8 +245,8 @@ dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid
  * the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.
  */
-#define DG_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
-#define DG_NOALLOC_MAX_UV_OVERSAMPLE 16384
+#define DG_NOALLOC_SCRATCH_BYTES (1024u * 1024u)
+#define DG_NOALLOC_MAX_UV_OVERSAMPLE (1 << 20)
 #define DG_NOALLOC_MAX_W_OVERSAMPLE 512
 #define DG_NOALLOC_MAX_SUBGRIDS 1024
 #define DG_NOALLOC_MAX_VIS (1 << 25)

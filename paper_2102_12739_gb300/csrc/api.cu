@@ -7,8 +7,6 @@
 #include <new>
 #include <vector>
 
-#include <cudaTypedefs.h>
-
 #include "internal.cuh"
 
 cudaError_t dg_launch_pack(cudaStream_t st, dg_dtype dtype, int n_subgrids, int64_t elems,
@@ -82,37 +80,11 @@ void free_plan_buffers(degrid_plan *p)
     free_events(p);
     cudaFree(p->guv);
     cudaFree(p->gw);
-    cudaFree(p->guv2);
-    cudaFree(p->gw2);
     cudaFree(p->status);
     cudaFree(p->work_counter);
     cudaFree(p->n_chunks);
     cudaFree(p->prefix);
     cudaFree(p->chunks);
-}
-
-// TMA descriptor of a row-major FP32 table [rows][cols]; one box = one row,
-// as tile::gather4 requires.
-dg_status encode_row_table(CUtensorMap *tm, float *table, int rows, int cols)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return DG_ERR_CUDA;
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)cols, 1};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, table, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_64B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? DG_OK : DG_ERR_CUDA;
 }
 
 // Grows the schedule scratch so that S subgrids and n_vis visibilities fit.
@@ -167,14 +139,18 @@ struct KernelTimer {
     }
 };
 
-int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int max_per_sm)
+// Persistent grid: the resident CTAs of every SM, but no more CTAs than
+// there are chunks for their chunk-claiming warps.
+int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int max_per_sm, int claimers_per_block)
 {
     int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : max_per_sm;
     if (per_sm < 1)
         per_sm = 1;
+    if (per_sm > max_per_sm)
+        per_sm = max_per_sm;
     int64_t blocks = (int64_t)p->sm_count * per_sm;
     const int64_t max_chunks = n_vis / p->chunk + S;
-    const int64_t useful = (max_chunks + p->warps_per_block - 1) / p->warps_per_block;
+    const int64_t useful = (max_chunks + claimers_per_block - 1) / claimers_per_block;
     if (blocks > useful)
         blocks = useful;
     return blocks < 1 ? 1 : (int)blocks;
@@ -245,8 +221,8 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     p->geo.log2_w_os = l2w;
     p->geo.row_stride = nx * nz;
     p->geo.plane = (int64_t)nx * ny * nz;
-    // small w tables (32 bytes per duplicated row) live in each CTA's shared memory
-    p->geo.w_table_rows = (size_t)w_oversample * 2 * w_support * sizeof(float) <= 16 * 1024 ? w_oversample : 0;
+    // small w tables (16 bytes per row) live in each CTA's shared memory
+    p->geo.w_table_rows = (size_t)w_oversample * w_support * sizeof(float) <= 8 * 1024 ? w_oversample : 0;
     p->uv_oversample = uv_oversample;
     p->w_oversample = w_oversample;
     p->dtype = dtype;
@@ -260,17 +236,8 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
         h_uv[i] = (float)g_uv[i];            // round to nearest
     for (size_t i = 0; i < h_w.size(); ++i)
         h_w[i] = (float)g_w[i];
-    // the same values with every tap stored twice: (g, g) pairs are ready
-    // operands of the packed FP32 FMAs of the degridding kernel
-    std::vector<float> h_uv2(2 * h_uv.size()), h_w2(2 * h_w.size());
-    for (size_t i = 0; i < h_uv.size(); ++i)
-        h_uv2[2 * i] = h_uv2[2 * i + 1] = h_uv[i];
-    for (size_t i = 0; i < h_w.size(); ++i)
-        h_w2[2 * i] = h_w2[2 * i + 1] = h_w[i];
     if ((st = dev_alloc(&p->guv, h_uv.size())) != DG_OK ||
         (st = dev_alloc(&p->gw, h_w.size())) != DG_OK ||
-        (st = dev_alloc(&p->guv2, h_uv2.size())) != DG_OK ||
-        (st = dev_alloc(&p->gw2, h_w2.size())) != DG_OK ||
         (st = dev_alloc(&p->status, 1)) != DG_OK ||
         (st = dev_alloc(&p->work_counter, 1)) != DG_OK ||
         (st = dev_alloc(&p->n_chunks, 1)) != DG_OK) {
@@ -282,10 +249,6 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     if (e == cudaSuccess)
         e = cudaMemcpy(p->gw, h_w.data(), sizeof(float) * h_w.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(p->guv2, h_uv2.data(), sizeof(float) * h_uv2.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(p->gw2, h_w2.data(), sizeof(float) * h_w2.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
         e = cudaMemset(p->status, 0, sizeof(dg::DeviceStatus));
     if (e == cudaSuccess)
         e = cudaMemset(p->work_counter, 0, sizeof(int));
@@ -295,12 +258,6 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
         free_plan_buffers(p);
         delete p;
         return from_cuda(e);
-    }
-    if ((st = encode_row_table(&p->tm_uv2, p->guv2, uv_oversample, 2 * uv_support)) != DG_OK ||
-        (st = encode_row_table(&p->tm_w2, p->gw2, w_oversample, 2 * w_support)) != DG_OK) {
-        free_plan_buffers(p);
-        delete p;
-        return st;
     }
     *out = p;
     return DG_OK;
@@ -440,7 +397,7 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
         return from_cuda(e);
     if (p->max_blocks_degrid == 0)
         p->max_blocks_degrid = dg_max_blocks_per_sm_degrid(p);
-    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_degrid);
+    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_degrid, p->warps_per_block);
     KernelTimer timer(p, s);
     e = dg_launch_degrid(p, s, subgrids, subgrid_scale, uvw, vis_offsets, vis_out, blocks);
     timer.stop();
@@ -480,7 +437,7 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
         return from_cuda(e);
     if (p->max_blocks_adjoint == 0)
         p->max_blocks_adjoint = dg_max_blocks_per_sm_adjoint(p);
-    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_adjoint);
+    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_adjoint, p->warps_per_block);
     KernelTimer timer(p, s);
     e = dg_launch_adjoint(p, s, uvw, vis_offsets, vis_in, sub_out, blocks);
     timer.stop();

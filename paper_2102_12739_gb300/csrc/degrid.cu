@@ -2,82 +2,65 @@
 // variants), re-designed for sm_103a.
 //
 // Work decomposition.  A persistent grid of warps claims chunks of
-// consecutive visibilities of one subgrid (schedule.cu) and walks each chunk
-// in batches of 32 visibilities.  Claims are pipelined: a warp holds the
-// descriptor of its next chunk while working on the current one.
-//
-// Per batch, three stages overlap across consecutive batches of a warp:
+// consecutive visibilities of one subgrid (schedule.cu, claims pipelined one
+// chunk ahead) and walks each chunk in batches of 32 visibilities.  Per batch
+// three stages overlap across consecutive batches of a warp:
 //  1. the FP64 coordinates of batch n + 2 are loaded into registers;
 //  2. for batch n + 1, lane i snaps visibility i (exact integer rint of the
-//     coordinates, internal.cuh) and the warp fetches the three GCF rows of
-//     every visibility with TMA tile::gather4 copies (4 table rows per copy)
-//     into the warp's shared-memory stage, completion tracked by an mbarrier;
+//     coordinates, internal.cuh), records its footprint key and w-kernel row
+//     and copies its g_u and g_v rows into the warp's shared-memory stage with
+//     cp.async (the small w table lives in shared memory).  The paper's D1
+//     likewise computes all coordinates of its N_b visibilities cooperatively
+//     into shared memory before the sums;
 //  3. batch n is summed from the stage that arrived.
-// The paper's D1 computes the coordinates of its N_b visibilities
-// cooperatively into shared memory first; here that step is both overlapped
-// with the sums and taken off the load/store pipe by the TMA engine.
 //
-// Footprint sum.  Each quarter-warp (8 lanes) computes one visibility; the
-// warp does 4 visibilities per step, 8 steps per batch.  Lane (a-pair, c-pair)
-// holds the 4 footprint columns (a0 + i, c0 + j), i, j in {0, 1}, of all 8
-// rows b in registers (32 complex values) and reloads them only when the
-// footprint start changes: consecutive visibilities of a dense list share the
-// footprint (the reuse the paper notes for D1), so the subgrid is read once
-// per footprint.  Each lane accumulates along v (b) as in D1, with one packed
-// FP32 FMA (FFMA2) per complex x real product; the GCF tables are stored with
-// every tap duplicated, so a 16-byte shared load yields two ready (g, g)
-// operand pairs.  The four column sums are then weighted by g_u and g_w.
-// A batch whose 32 visibilities share one valid footprint takes a branch-free
-// path; otherwise every quarter checks and reloads its own footprint.
+// Footprint sum.  The separable weights let the 8 x 8 x 4 sum be taken in
+// three contractions,
+//     V = sum_b g_v[b] sum_a g_u[a] M[b][a],   M[b][a] = sum_c g_w[c] s[y0+b][x0+a][z0+c],
+// and M depends only on the footprint start and the w-kernel row.  On a dense
+// list hundreds of consecutive visibilities share both (the reuse the paper
+// notes for D1), so M is computed once per run and each visibility then costs
+// 72 complex x real products instead of 256.  Each quarter-warp computes one
+// visibility (4 per step, 8 steps per batch); lane q of a quarter keeps the
+// column M[0..7][q] in registers, accumulates along v (b) as D1 does, and
+// scales by g_u[q].  A batch whose 32 visibilities share one footprint and
+// one w row takes a branch-free path; otherwise each quarter checks, and
+// rebuilds its M when its visibility needs another one (so every input is
+// handled, at up to 82 products per visibility when nothing is shared).
+// Scalar FP32 FMAs: packed FFMA2 with three distinct register pairs ran at
+// about half the FP32 peak on this part.
 //
 // Reduction and output.  The 8 partials of a quarter are reduced with a
 // transposing butterfly (3 shuffle levels that halve the live values), after
 // which every lane holds one whole visibility; the warp writes its 32
-// results into one contiguous 256-byte segment (the paper's bulk
-// contiguous write-out, without the shared-memory staging).
+// results into one contiguous 256-byte segment (the paper's bulk contiguous
+// write-out, without the shared-memory staging).
 #include "internal.cuh"
 
 namespace dg {
 namespace {
 
-#ifndef DG_STAGING_TMA
-#define DG_STAGING_TMA 0     // GCF rows staged by TMA tile::gather4 (1) or cp.async (0)
+#ifndef DG_DEGRID_MIN_BLOCKS
+#define DG_DEGRID_MIN_BLOCKS 3   // resident CTAs per SM the register budget is sized for
 #endif
 
-#ifndef DG_DEGRID_MAX_WARPS
-#define DG_DEGRID_MAX_WARPS 8
-#endif
-#ifndef DG_PINNED_UVW_LOADS
-#define DG_PINNED_UVW_LOADS 1
-#endif
-#ifndef DG_FOOTPRINT_ASM_LOADS
-#define DG_FOOTPRINT_ASM_LOADS 1   // footprint loads the compiler may not re-issue
-#endif
-
-constexpr int kMaxWarps = DG_DEGRID_MAX_WARPS;   // per CTA
-constexpr int kBatch = 32;                  // visibilities per warp batch
-constexpr int kUVRow = 16;                  // floats per duplicated uv row (64 B)
-constexpr int kWRow = 8;                    // floats per duplicated w row (32 B)
-constexpr unsigned kStageBytes = kBatch * 2 * kUVRow * 4;  // TMA bytes per batch: g_u + g_v rows
-// The duplicated w table (O_w rows of 32 B) is kept in every CTA's shared
-// memory when it is at most this large (O_w <= 512); otherwise its rows are
-// fetched per batch like the uv rows.  Along a dense list f_w stays constant
-// for thousands of visibilities, so per-batch w fetches would make every warp
-// on the GPU hit the same few L2 lines.
-constexpr int kMaxWTableBytes = 16 * 1024;
+constexpr int kMaxWarps = 8;                // per CTA
+constexpr int kBatch = 32;                  // visibilities per batch
+constexpr int kUVRow = 8;                   // floats per uv table row (32 B)
+constexpr int kWRow = 4;                    // floats per w table row (16 B)
 
 struct alignas(128) Stage {
-    float gu[kBatch][kUVRow];   // TMA destination: g_uv[fu] duplicated
-    float gv[kBatch][kUVRow];   // TMA destination: g_uv[fv] duplicated
-    float gw[kBatch][kWRow];    // TMA destination: g_w[fw] duplicated
+    float gu[kBatch][kUVRow];   // g_uv[fu], per visibility
+    float gv[kBatch][kUVRow];   // g_uv[fv]
+    float gw[kBatch][kWRow];    // g_w[fw]
     int key[kBatch];            // footprint start (y0 * nx + x0) * nz + z0, -1 invalid
-    int meta;                   // common key if all 32 share one valid footprint, else -1
+    int fw[kBatch];             // w-kernel row
+    int uniform;                // all 32 share one valid footprint and one w row
 };
 
 struct alignas(128) WarpSmem {
     Stage st[2];
-    float2 slow[8][kWarp];      // per-step partials on the mixed-footprint path
-    unsigned long long bar[2];  // one mbarrier per stage
+    float2 part[8][kWarp];      // per-step partials on the mixed path
 };
 
 // ---- PTX wrappers ---------------------------------------------------------
@@ -85,62 +68,6 @@ struct alignas(128) WarpSmem {
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (int i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, parity))
-            return true;
-    return false;
-}
-
-// Four rows (r0..r3) of a 2D tensor, column 0, into consecutive shared
-// memory rows; completion counted in bytes on `bar`.
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *tm, int r0, int r1,
-                                            int r2, int r3, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
-        : "memory");
 }
 
 // 16-byte asynchronous global -> shared copy (L2 only), grouped per batch.
@@ -154,90 +81,47 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+// ---- the factored sum -------------------------------------------------------
 
-// ---- footprint registers ----------------------------------------------------
-
-// One footprint sample as (re, im).  The loads are volatile inline PTX so
-// that, under register pressure, the compiler keeps (or spills) the values
-// instead of re-issuing read-only global loads inside the hot loop.
+// M[b] = sum_c g_w[c] s[y0 + b][x0 + q][z0 + c] for b = 0..7 (this lane's
+// column q of the footprint with origin `key` in the subgrid at `base`).
 template <int DT>
-__device__ __forceinline__ float2 load_sample(const void *sub, int64_t i)
+__device__ __forceinline__ void build_column(float2 (&M)[8], const void *sub, int64_t base, int key,
+                                             int q, const float4 &gw, const Geometry &g)
 {
-#if DG_FOOTPRINT_ASM_LOADS
-    if (DT == DG_C64) {
-        float2 v;
-        asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];"
-                     : "=f"(v.x), "=f"(v.y)
-                     : "l"(reinterpret_cast<const float2 *>(sub) + i));
-        return v;
-    } else {
-        unsigned u;
-        asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(reinterpret_cast<const unsigned *>(sub) + i));
-        if (DT == DG_C32_F16) {
-            __half2 h = *reinterpret_cast<const __half2 *>(&u);
-            return __half22float2(h);
-        }
-        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
-    }
-#else
-    return Storage<DT>::load(sub, i);
-#endif
-}
-
-// B[k][e][i][j] = s[y0 + b][x0 + a0 + i][z0 + c0 + j] with b = 2 * ((k + quarter) & 3) + e.
-// The row order is rotated by quarter so that, at every shared-memory load of
-// a step, the four quarters read different 16-byte chunks of their g_v rows
-// (no bank conflicts), while the register slots stay compile-time indices.
-template <int DT>
-__device__ __forceinline__ void load_footprint(float2 (&B)[4][2][2][2], const void *sub,
-                                               int64_t base, int key, int quarter, int a0, int c0,
-                                               const Geometry &g)
-{
+    const int64_t col = base + key + (int64_t)q * g.nz;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int j4 = (k + quarter) & 3;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int64_t row = base + key + (int64_t)(2 * j4 + e) * g.row_stride;
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    B[k][e][i][j] = load_sample<DT>(sub, row + (a0 + i) * g.nz + (c0 + j));
-        }
+    for (int b = 0; b < 8; ++b) {
+        const int64_t e = col + (int64_t)b * g.row_stride;
+        const float2 s0 = Storage<DT>::load(sub, e), s1 = Storage<DT>::load(sub, e + 1);
+        const float2 s2 = Storage<DT>::load(sub, e + 2), s3 = Storage<DT>::load(sub, e + 3);
+        M[b].x = fmaf(s3.x, gw.w, fmaf(s2.x, gw.z, fmaf(s1.x, gw.y, s0.x * gw.x)));
+        M[b].y = fmaf(s3.y, gw.w, fmaf(s2.y, gw.z, fmaf(s1.y, gw.y, s0.y * gw.x)));
     }
 }
 
-// Partial sum of visibility r of the stage over this lane's 4 columns:
-// sum_b g_v[b] * (g_u[a0] g_w[c0] B(a0,c0) + ...), 38 packed FP32 operations.
-__device__ __forceinline__ float2 footprint_step(const float2 (&B)[4][2][2][2], const Stage &S,
-                                                 int r, int quarter, int ap, int cp)
+// This lane's part of visibility r: g_u[q] * sum_b g_v[b] M[b] (18 FP32 ops).
+__device__ __forceinline__ float2 apply_column(const float2 (&M)[8], const Stage &S, int r, int q)
 {
-    const float4 *gvrow = reinterpret_cast<const float4 *>(S.gv[r]);
-    float2 acc[2][2];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 gk = gvrow[(k + quarter) & 3];
-        const float2 g0 = lo2(gk), g1 = hi2(gk);
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                acc[i][j] = k == 0 ? __fmul2_rn(B[0][0][i][j], g0)
-                                   : __ffma2_rn(B[k][0][i][j], g0, acc[i][j]);
-                acc[i][j] = __ffma2_rn(B[k][1][i][j], g1, acc[i][j]);
-            }
-    }
-    const float4 gu4 = reinterpret_cast<const float4 *>(S.gu[r])[ap];
-    const float4 gw4 = reinterpret_cast<const float4 *>(S.gw[r])[cp];
-    float2 t0 = __fmul2_rn(acc[0][0], lo2(gu4));
-    t0 = __ffma2_rn(acc[1][0], hi2(gu4), t0);
-    float2 t1 = __fmul2_rn(acc[0][1], lo2(gu4));
-    t1 = __ffma2_rn(acc[1][1], hi2(gu4), t1);
-    float2 p = __fmul2_rn(t0, lo2(gw4));
-    return __ffma2_rn(t1, hi2(gw4), p);
+    const float4 v0 = reinterpret_cast<const float4 *>(S.gv[r])[0];
+    const float4 v1 = reinterpret_cast<const float4 *>(S.gv[r])[1];
+    const float gu = S.gu[r][q];
+    float re = M[0].x * v0.x, im = M[0].y * v0.x;
+    re = fmaf(M[1].x, v0.y, re);
+    im = fmaf(M[1].y, v0.y, im);
+    re = fmaf(M[2].x, v0.z, re);
+    im = fmaf(M[2].y, v0.z, im);
+    re = fmaf(M[3].x, v0.w, re);
+    im = fmaf(M[3].y, v0.w, im);
+    re = fmaf(M[4].x, v1.x, re);
+    im = fmaf(M[4].y, v1.x, im);
+    re = fmaf(M[5].x, v1.y, re);
+    im = fmaf(M[5].y, v1.y, im);
+    re = fmaf(M[6].x, v1.z, re);
+    im = fmaf(M[6].y, v1.z, im);
+    re = fmaf(M[7].x, v1.w, re);
+    im = fmaf(M[7].y, v1.w, im);
+    return make_float2(re * gu, im * gu);
 }
 
 // Transposing butterfly over the 8 lanes of a quarter: on entry P[t] is this
@@ -259,7 +143,7 @@ __device__ __forceinline__ float2 quarter_reduce(float2 (&P)[8], int q)
     return P[0];
 }
 
-// ---- batch stream ---------------------------------------------------------
+// ---- batch stream -----------------------------------------------------------
 
 struct Batch {
     int s;          // subgrid
@@ -268,6 +152,9 @@ struct Batch {
     long long end;  // end of the chunk
 };
 
+// Claims chunks with an atomic counter, one claim ahead: while a warp works
+// on a chunk it already holds the descriptor of the next one, and the atomic
+// for the one after that is in flight.
 struct Claimer {
     const Schedule &sched;
     int total;
@@ -324,123 +211,65 @@ struct Claimer {
     }
 };
 
-__device__ __forceinline__ void load_uvw(const double *__restrict__ uvw, const Batch &b, int lane,
-                                         double &u, double &v, double &w)
+struct Coords3 {
+    double u, v, w;
+};
+
+__device__ __forceinline__ Coords3 load_uvw(const double *__restrict__ uvw, const Batch &b, int lane)
 {
+    Coords3 c{0.0, 0.0, 0.0};
     if (lane < b.n) {
         const double *p = uvw + 3 * (b.b0 + lane);
-#if DG_PINNED_UVW_LOADS
-        // volatile: the loads stay where they are issued (two batches ahead of
-        // their use) instead of being sunk to the use under register pressure
-        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(u) : "l"(p));
-        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p + 1));
-        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(w) : "l"(p + 2));
-#else
-        u = __ldg(p);
-        v = __ldg(p + 1);
-        w = __ldg(p + 2);
-#endif
-    } else {
-        u = v = w = 0.0;
+        c.u = __ldg(p);
+        c.v = __ldg(p + 1);
+        c.w = __ldg(p + 2);
     }
+    return c;
 }
 
-// Stage 2 for one batch: coordinates, keys, and the copies of the three
-// duplicated GCF rows of every visibility into the stage.
-__device__ __forceinline__ void issue_batch(const Batch &b, double u, double v, double w,
-                                            const Geometry &g, Stage &S, uint32_t bar,
-                                            const CUtensorMap *tm_uv, const CUtensorMap *tm_w,
-                                            const float *__restrict__ guv2,
-                                            const float *__restrict__ gw2, const float4 *wtab,
+// Stage 2 of a batch: coordinates, keys, w rows and the copies of the g_u /
+// g_v rows (2 lanes per 32-byte row).
+__device__ __forceinline__ void issue_batch(const Batch &b, const Coords3 &c, const Geometry &g,
+                                            Stage &S, const float *__restrict__ guv,
+                                            const float *__restrict__ gwt, const float4 *wtab,
                                             int lane, DeviceStatus *status)
 {
     const bool in = lane < b.n;
     VisCoords vc;
-    const bool valid = in && visibility_coords(u, v, w, g, vc);
+    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
     const int key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
     const int fu = valid ? vc.fu : 0, fv = valid ? vc.fv : 0, fw = valid ? vc.fw : 0;
     S.key[lane] = key;
-    const int key0 = __shfl_sync(kFull, key, 0);
-    const bool uniform = __all_sync(kFull, key == key0) && key0 >= 0;
+    S.fw[lane] = fw;
+    const int key0 = __shfl_sync(kFull, key, 0), fw0 = __shfl_sync(kFull, fw, 0);
+    const bool uniform = __all_sync(kFull, key == key0 && fw == fw0) && key0 >= 0;
     if (lane == 0)
-        S.meta = uniform ? key0 : -1;
+        S.uniform = uniform;
     const unsigned bad = __ballot_sync(kFull, in && !valid);
     if (lane == 0 && bad)
         atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));
-    // g_w rows: from the CTA's copy of the table when there is one
-    if (wtab) {
-        float4 *dst = reinterpret_cast<float4 *>(S.gw[lane]);
-        dst[0] = wtab[2 * fw];
-        dst[1] = wtab[2 * fw + 1];
-    }
-#if DG_STAGING_TMA
-    (void)guv2;
-    (void)tm_w;
-    // lanes 0-7 gather g_u rows, 8-15 g_v rows, 4 rows per lane
-    const int grp = lane >> 3, jj = lane & 7;
-    int r[4];
+    if (wtab)
+        reinterpret_cast<float4 *>(S.gw)[lane] = wtab[fw];
+    else
+        cp_async16(smem_u32(S.gw[lane]), gwt + (size_t)fw * kWRow);
+    const int half = lane & 1;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int src = 4 * jj + m;
-        const int xu = __shfl_sync(kFull, fu, src);
-        const int xv = __shfl_sync(kFull, fv, src);
-        r[m] = grp == 0 ? xu : xv;
-    }
-    fence_proxy_async();
-    __syncwarp();
-    if (lane == 0)
-        mbar_arrive_expect_tx(bar, kStageBytes);
-    __syncwarp();
-    if (grp < 2)
-        tma_gather4(grp == 0 ? smem_u32(S.gu[4 * jj]) : smem_u32(S.gv[4 * jj]), tm_uv, r[0], r[1],
-                    r[2], r[3], bar);
-    if (!wtab) {
-        const int cw = lane & 1;
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int rr = (lane >> 1) + 16 * m;
-            const int xw = __shfl_sync(kFull, fw, rr);
-            cp_async16(smem_u32(&S.gw[rr][4 * cw]), gw2 + (size_t)xw * kWRow + 4 * cw);
-        }
-        cp_async_commit();
-    }
-#else
-    (void)bar;
-    (void)tm_uv;
-    (void)tm_w;
-    // 4 lanes per 64-byte uv row (one 16-byte chunk each), 2 per 32-byte w row
-    const int cu = lane & 3, cw = lane & 1;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int r = (lane >> 2) + 8 * m;
+    for (int m = 0; m < 2; ++m) {
+        const int r = (lane >> 1) + 16 * m;
         const int xu = __shfl_sync(kFull, fu, r);
         const int xv = __shfl_sync(kFull, fv, r);
-        cp_async16(smem_u32(&S.gu[r][4 * cu]), guv2 + (size_t)xu * kUVRow + 4 * cu);
-        cp_async16(smem_u32(&S.gv[r][4 * cu]), guv2 + (size_t)xv * kUVRow + 4 * cu);
-    }
-    if (!wtab) {
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const int r = (lane >> 1) + 16 * m;
-            const int xw = __shfl_sync(kFull, fw, r);
-            cp_async16(smem_u32(&S.gw[r][4 * cw]), gw2 + (size_t)xw * kWRow + 4 * cw);
-        }
+        cp_async16(smem_u32(&S.gu[r][4 * half]), guv + (size_t)xu * kUVRow + 4 * half);
+        cp_async16(smem_u32(&S.gv[r][4 * half]), guv + (size_t)xv * kUVRow + 4 * half);
     }
     cp_async_commit();
-#endif
 }
-
-#ifndef DG_DEGRID_MIN_BLOCKS
-#define DG_DEGRID_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
-#endif
 
 template <int DT>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_DEGRID_MIN_BLOCKS)
 degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *__restrict__ scale,
-              const double *__restrict__ uvw, const __grid_constant__ CUtensorMap tm_uv,
-              const __grid_constant__ CUtensorMap tm_w, const float *__restrict__ guv2,
-              const float *__restrict__ gw2, const Schedule sched,
-              float2 *__restrict__ vis_out, DeviceStatus *__restrict__ status)
+              const double *__restrict__ uvw, const float *__restrict__ guv,
+              const float *__restrict__ gwt, const Schedule sched, float2 *__restrict__ vis_out,
+              DeviceStatus *__restrict__ status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // [w table (optional)] [one WarpSmem per warp]
@@ -449,118 +278,83 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     const float4 *wtab = nullptr;
     if (wtab_bytes) {
         float4 *t = reinterpret_cast<float4 *>(smem_raw);
-        const float4 *src = reinterpret_cast<const float4 *>(gw2);
-        for (int i = threadIdx.x; i < g.w_table_rows * (kWRow / 4); i += blockDim.x)
+        const float4 *src = reinterpret_cast<const float4 *>(gwt);
+        for (int i = threadIdx.x; i < g.w_table_rows; i += blockDim.x)
             t[i] = __ldg(src + i);
         __syncthreads();
         wtab = t;
     }
     const int lane = threadIdx.x & 31;
-    const int quarter = lane >> 3, q = lane & 7, ap = q >> 1, cp = q & 1;
-    const int a0 = 2 * ap, c0 = 2 * cp;
-    const uint32_t bar0 = smem_u32(&ws.bar[0]), bar1 = smem_u32(&ws.bar[1]);
-    if (lane == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        fence_barrier_init();
-    }
-    __syncwarp();
+    const int quarter = lane >> 3, q = lane & 7;
 
     Claimer claimer(sched, lane);
-    Batch bB = claimer.claim();         // tables in flight
+    Batch bB = claimer.claim();         // rows in flight
     if (bB.n == 0)
         return;
-    double u, v, w;
-    load_uvw(uvw, bB, lane, u, v, w);
-    issue_batch(bB, u, v, w, g, ws.st[0], bar0, &tm_uv, &tm_w, guv2, gw2, wtab, lane, status);
+    issue_batch(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, gwt, wtab, lane, status);
     Batch bC = claimer.advance(bB);     // coordinates in registers
-    load_uvw(uvw, bC, lane, u, v, w);
+    Coords3 cC = load_uvw(uvw, bC, lane);
 
-    uint32_t parity = 0;                // bit s: parity of the next phase of stage s
     int stage = 0;
-    int cur = -2, cur_s = -1;           // footprint held in B (key, subgrid)
-    float2 B[4][2][2][2];
+    float2 M[8];                        // footprint column M[0..7][q] of (m_key, m_fw, m_s)
+    int m_key = -2, m_fw = -1, m_s = -1;
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int e = 0; e < 2; ++e)
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    B[k][e][i][j] = make_float2(0.f, 0.f);
+    for (int b = 0; b < 8; ++b)
+        M[b] = make_float2(0.f, 0.f);
 
     while (bB.n > 0) {
-        const Batch bA = bB;            // computed in this iteration
+        const Batch bA = bB;            // summed in this iteration
         const int sA = stage;
         bB = bC;
         if (bB.n > 0)
-            issue_batch(bB, u, v, w, g, ws.st[sA ^ 1], sA ? bar0 : bar1, &tm_uv, &tm_w, guv2, gw2,
-                        wtab, lane, status);
+            issue_batch(bB, cC, g, ws.st[sA ^ 1], guv, gwt, wtab, lane, status);
         bC = claimer.advance(bC);
-        load_uvw(uvw, bC, lane, u, v, w);
-
-#if DG_STAGING_TMA
-        if (!mbar_wait(sA ? bar1 : bar0, (parity >> sA) & 1)) {
-            if (lane == 0)
-                atomicOr(&status->flags, kFlagTimeout);
-            if (bB.n > 0)       // let the copies already issued land before leaving
-                mbar_wait(sA ? bar0 : bar1, (parity >> (sA ^ 1)) & 1);
-            return;
-        }
-        parity ^= 1u << sA;
-        if (!wtab) {
-            if (bB.n > 0)
-                cp_async_wait<1>();
-            else
-                cp_async_wait<0>();
-        }
-        __syncwarp();
-#else
+        cC = load_uvw(uvw, bC, lane);
         if (bB.n > 0)
-            cp_async_wait<1>();     // the stage of batch A; batch B may stay in flight
+            cp_async_wait<1>();         // the stage of batch A; batch B may stay in flight
         else
             cp_async_wait<0>();
         __syncwarp();
-#endif
 
         const Stage &S = ws.st[sA];
-        if (bA.s != cur_s) {
-            cur_s = bA.s;
-            cur = -2;
+        if (bA.s != m_s) {
+            m_s = bA.s;
+            m_key = -2;
         }
         const int64_t base = (int64_t)bA.s * g.plane;
         float2 P[8];
-        const int meta = S.meta;
-        if (meta >= 0) {
-            if (meta != cur) {
-                load_footprint<DT>(B, subgrids, base, meta, quarter, a0, c0, g);
-                cur = meta;
+        if (S.uniform) {
+            const int k0 = S.key[0], f0 = S.fw[0];
+            if (k0 != m_key || f0 != m_fw) {
+                build_column<DT>(M, subgrids, base, k0, q, reinterpret_cast<const float4 *>(S.gw)[0], g);
+                m_key = k0;
+                m_fw = f0;
             }
 #pragma unroll
             for (int t = 0; t < 8; ++t)
-                P[t] = footprint_step(B, S, 4 * t + quarter, quarter, ap, cp);
+                P[t] = apply_column(M, S, 4 * t + quarter, q);
         } else {
 #pragma unroll 1
             for (int t = 0; t < 8; ++t) {
                 const int r = 4 * t + quarter;
-                const int kv = S.key[r];
-                if (kv != cur) {
-                    cur = kv;
-                    if (kv >= 0)
-                        load_footprint<DT>(B, subgrids, base, kv, quarter, a0, c0, g);
+                const int kv = S.key[r], fv = S.fw[r];
+                if (kv >= 0 && (kv != m_key || fv != m_fw)) {
+                    build_column<DT>(M, subgrids, base, kv, q, reinterpret_cast<const float4 *>(S.gw)[r], g);
+                    m_key = kv;
+                    m_fw = fv;
                 }
-                ws.slow[t][lane] = kv >= 0 ? footprint_step(B, S, r, quarter, ap, cp)
-                                           : make_float2(0.f, 0.f);
+                ws.part[t][lane] = kv >= 0 ? apply_column(M, S, r, q) : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int t = 0; t < 8; ++t)
-                P[t] = ws.slow[t][lane];
+                P[t] = ws.part[t][lane];
         }
         float2 V = quarter_reduce(P, q);
         const int r_out = 4 * q + quarter;
-        if (DT != DG_C64)
-            V = __fmul2_rn(V, make_float2(__ldg(scale + bA.s), __ldg(scale + bA.s)));
+        if (DT != DG_C64) {
+            const float sc = __ldg(scale + bA.s);
+            V = __fmul2_rn(V, make_float2(sc, sc));
+        }
         if (r_out < bA.n)
             vis_out[bA.b0 + r_out] = V;
         __syncwarp();
@@ -570,7 +364,9 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
 
 size_t smem_bytes(const degrid_plan *p, int warps)
 {
-    const size_t wt = p->geo.w_table_rows > 0 ? ((size_t)p->geo.w_table_rows * kWRow * 4 + 127) & ~(size_t)127 : 0;
+    const size_t wt = p->geo.w_table_rows > 0
+                          ? ((size_t)p->geo.w_table_rows * kWRow * 4 + 127) & ~(size_t)127
+                          : 0;
     return wt + sizeof(WarpSmem) * (size_t)warps;
 }
 
@@ -584,9 +380,8 @@ cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const 
                                          (int)smem);
     if (e != cudaSuccess)
         return e;
-    degrid_kernel<DT><<<grid_blocks, threads, smem, st>>>(p->geo, subgrids, scale, uvw, p->tm_uv2,
-                                                           p->tm_w2, p->guv2, p->gw2, sched, out,
-                                                           p->status);
+    degrid_kernel<DT><<<grid_blocks, threads, smem, st>>>(p->geo, subgrids, scale, uvw, p->guv,
+                                                           p->gw, sched, out, p->status);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,6 @@
 // Internal definitions shared by the CUDA translation units of the library.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -151,10 +150,6 @@ struct degrid_plan {
     dg_dtype dtype;
     float *guv;                 // device FP32 [uv_os][8]
     float *gw;                  // device FP32 [w_os][4]
-    float *guv2;                // device FP32 [uv_os][8][2]: every tap twice
-    float *gw2;                 // device FP32 [w_os][4][2]
-    CUtensorMap tm_uv2;         // TMA descriptors of guv2 / gw2 (rows of 64 / 32 B)
-    CUtensorMap tm_w2;
     dg::DeviceStatus *status;   // device
     int *work_counter;          // device [1]
     int *n_chunks;              // device [1]
@@ -182,5 +177,5 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
 cudaError_t dg_launch_coords(degrid_plan *p, cudaStream_t st, const double *uvw,
                              int64_t n_vis, int32_t *coords_out);
 int dg_max_blocks_per_sm_degrid(degrid_plan *p);
-int dg_max_warps_per_block();   // largest CTA the kernels are compiled for
+int dg_max_warps_per_block();        // largest warps_per_block the kernels are built for
 int dg_max_blocks_per_sm_adjoint(degrid_plan *p);

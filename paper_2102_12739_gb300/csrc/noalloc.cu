@@ -8,9 +8,9 @@
 // budget is owned by another allocator, where a library that allocates on
 // its own is not allowed.  degrid_execute_noalloc therefore needs no plan: the
 // caller passes the GCF tables and every input and output as device
-// pointers, and all scratch the kernels need (duplicated GCF taps, the chunk
-// schedule, the work counter and the status words) comes from the fixed,
-// file-scope array below.  Every GPU that loads the library holds this array
+// pointers, and all scratch the kernels need (the chunk schedule, the work
+// counter and the status words) comes from the fixed, file-scope array
+// below.  Every GPU that loads the library holds this array
 // until the process exits.
 #include <mutex>
 
@@ -23,16 +23,12 @@ cudaError_t dg_launch_degrid(degrid_plan *p, cudaStream_t st, const void *subgri
 namespace {
 
 // Scratch layout, in bytes from the start of the array.
-constexpr size_t kUV2Bytes = (size_t)DG_NOALLOC_MAX_UV_OVERSAMPLE * 16 * sizeof(float);
-constexpr size_t kW2Bytes = (size_t)DG_NOALLOC_MAX_W_OVERSAMPLE * 8 * sizeof(float);
 constexpr int kChunk = 1024;    // visibilities per work item in this entry point
 constexpr size_t kMaxChunks =
     ((size_t)DG_NOALLOC_MAX_VIS + kChunk - 1) / kChunk + DG_NOALLOC_MAX_SUBGRIDS + 1;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t kOffUV2 = 0;
-constexpr size_t kOffW2 = align256(kOffUV2 + kUV2Bytes);
-constexpr size_t kOffChunks = align256(kOffW2 + kW2Bytes);
+constexpr size_t kOffChunks = 0;
 constexpr size_t kOffPrefix = align256(kOffChunks + kMaxChunks * sizeof(dg::ChunkDesc));
 constexpr size_t kOffCounters = align256(kOffPrefix + (DG_NOALLOC_MAX_SUBGRIDS + 1) * sizeof(int));
 constexpr size_t kOffStatus = align256(kOffCounters + 2 * sizeof(int));
@@ -62,15 +58,6 @@ dg_status scratch_address(int device, unsigned char **out)
     }
     *out = g_scratch_dev[device];
     return DG_OK;
-}
-
-// FP32 table [rows][cols] -> the same values with every entry twice.
-__global__ void duplicate_taps(const float *__restrict__ src, int n, float2 *__restrict__ dst)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float v = src[i];
-        dst[i] = make_float2(v, v);
-    }
 }
 
 int log2_exact(int x)
@@ -137,12 +124,12 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
     p.geo.log2_w_os = l2w;
     p.geo.row_stride = nx * nz;
     p.geo.plane = (int64_t)nx * ny * nz;
-    p.geo.w_table_rows = w_oversample;          // at most 512 rows: staged in shared memory
+    p.geo.w_table_rows = w_oversample;          // at most 512 rows (8 KiB): staged in shared memory
     p.uv_oversample = uv_oversample;
     p.w_oversample = w_oversample;
     p.dtype = dtype;
-    p.guv2 = reinterpret_cast<float *>(scratch + kOffUV2);
-    p.gw2 = reinterpret_cast<float *>(scratch + kOffW2);
+    p.guv = const_cast<float *>(g_uv);
+    p.gw = const_cast<float *>(g_w);
     p.chunks = reinterpret_cast<dg::ChunkDesc *>(scratch + kOffChunks);
     p.prefix = reinterpret_cast<int *>(scratch + kOffPrefix);
     p.n_chunks = reinterpret_cast<int *>(scratch + kOffCounters);
@@ -160,11 +147,6 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
     // start at zero (the scheduler zeroes the work counter itself).
     cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(dg::DeviceStatus), s);
     if (e != cudaSuccess || n_vis == 0)
-        return from_cuda(e);
-    const int n_uv = uv_oversample * 8, n_w = w_oversample * 4;
-    duplicate_taps<<<(n_uv + 255) / 256, 256, 0, s>>>(g_uv, n_uv, reinterpret_cast<float2 *>(p.guv2));
-    duplicate_taps<<<(n_w + 255) / 256, 256, 0, s>>>(g_w, n_w, reinterpret_cast<float2 *>(p.gw2));
-    if ((e = cudaGetLastError()) != cudaSuccess)
         return from_cuda(e);
     e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, p.chunk, p.prefix, p.n_chunks,
                             p.chunks, p.cap_chunks, p.work_counter, p.status);

@@ -98,9 +98,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                     p, p, too_many_vis, p, None)
     assert rc == _native.DG_ERR_SCRATCH_LIMIT
     assert "scratch" in _native.status_string(rc)
-    rc = lib.degrid_execute_noalloc(None, 512, 512, 4, p, 32768, p, 128, _native.DG_C64, 1, p, None,
+    rc = lib.degrid_execute_noalloc(None, 512, 512, 4, p, 16384, p, 1024, _native.DG_C64, 1, p, None,
                                     p, p, 10, p, None)
-    assert rc == _native.DG_ERR_SCRATCH_LIMIT
+    assert rc == _native.DG_ERR_SCRATCH_LIMIT      # w table beyond the 512 rows it stages
     rc = lib.degrid_execute_noalloc(None, 512, 512, 4, p, 16384, p, 128, _native.DG_C64, 1025, p,
                                     None, p, p, 10, p, None)
     assert rc == _native.DG_ERR_SCRATCH_LIMIT
