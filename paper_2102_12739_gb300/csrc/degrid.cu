@@ -1,17 +1,12 @@
 // Degridding kernel (paper Section "Implementation": kernel D1 and its
 // variants), re-designed for sm_103a.
 //
-// Work decomposition.  A persistent grid of warps claims chunks of
-// consecutive visibilities of one subgrid (schedule.cu, claims pipelined one
-// chunk ahead) and walks each chunk in batches of 32 visibilities.  Per batch
+// Work decomposition (pipeline.cuh).  A persistent grid of warps walks chunks
+// of consecutive visibilities of one subgrid in batches of 32.  Per batch
 // three stages overlap across consecutive batches of a warp:
 //  1. the FP64 coordinates of batch n + 2 are loaded into registers;
-//  2. for batch n + 1, lane i snaps visibility i (exact integer rint of the
-//     coordinates, internal.cuh), records its footprint key and w-kernel row
-//     and copies its g_u and g_v rows into the warp's shared-memory stage with
-//     cp.async (the small w table lives in shared memory).  The paper's D1
-//     likewise computes all coordinates of its N_b visibilities cooperatively
-//     into shared memory before the sums;
+//  2. batch n + 1 is snapped and its GCF rows are copied into the warp's
+//     shared-memory stage with cp.async;
 //  3. batch n is summed from the stage that arrived.
 //
 // Footprint sum.  The separable weights let the 8 x 8 x 4 sum be taken in
@@ -35,7 +30,7 @@
 // which every lane holds one whole visibility; the warp writes its 32
 // results into one contiguous 256-byte segment (the paper's bulk contiguous
 // write-out, without the shared-memory staging).
-#include "internal.cuh"
+#include "pipeline.cuh"
 
 namespace dg {
 namespace {
@@ -45,41 +40,10 @@ namespace {
 #endif
 
 constexpr int kMaxWarps = 8;                // per CTA
-constexpr int kBatch = 32;                  // visibilities per batch
-constexpr int kUVRow = 8;                   // floats per uv table row (32 B)
-constexpr int kWRow = 4;                    // floats per w table row (16 B)
-
-struct alignas(128) Stage {
-    float gu[kBatch][kUVRow];   // g_uv[fu], per visibility
-    float gv[kBatch][kUVRow];   // g_uv[fv]
-    float gw[kBatch][kWRow];    // g_w[fw]
-    int key[kBatch];            // footprint start (y0 * nx + x0) * nz + z0, -1 invalid
-    int fw[kBatch];             // w-kernel row
-    int uniform;                // all 32 share one valid footprint and one w row
-};
-
 struct alignas(128) WarpSmem {
     Stage st[2];
     float2 part[8][kWarp];      // per-step partials on the mixed path
 };
-
-// ---- PTX wrappers ---------------------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// 16-byte asynchronous global -> shared copy (L2 only), grouped per batch.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---- the factored sum -------------------------------------------------------
 
@@ -143,127 +107,6 @@ __device__ __forceinline__ float2 quarter_reduce(float2 (&P)[8], int q)
     return P[0];
 }
 
-// ---- batch stream -----------------------------------------------------------
-
-struct Batch {
-    int s;          // subgrid
-    int n;          // visibilities in this batch (1..32), 0 = none
-    long long b0;   // first visibility
-    long long end;  // end of the chunk
-};
-
-// Claims chunks with an atomic counter, one claim ahead: while a warp works
-// on a chunk it already holds the descriptor of the next one, and the atomic
-// for the one after that is in flight.
-struct Claimer {
-    const Schedule &sched;
-    int total;
-    int lane;
-    int pend;           // lane 0: atomic result not yet consumed
-    ChunkDesc next;     // descriptor of the chunk after the current one
-    int next_valid;
-
-    __device__ Claimer(const Schedule &sc, int lane_) : sched(sc), lane(lane_)
-    {
-        total = *sc.n_chunks;
-        int a = 0, b = 0;
-        if (lane == 0) {
-            a = atomicAdd(sc.work_counter, 1);
-            b = atomicAdd(sc.work_counter, 1);
-        }
-        a = __shfl_sync(kFull, a, 0);
-        pend = b;
-        next_valid = a < total;
-        if (next_valid)
-            next = sc.chunks[a];
-    }
-
-    // Start the next claimed chunk; returns its first batch (n = 0 when done).
-    __device__ Batch claim()
-    {
-        Batch bt{0, 0, 0, 0};
-        if (!next_valid)
-            return bt;
-        const ChunkDesc cur = next;
-        const int k = __shfl_sync(kFull, pend, 0);
-        next_valid = k < total;
-        if (next_valid)
-            next = sched.chunks[k];
-        if (lane == 0)
-            pend = atomicAdd(sched.work_counter, 1);
-        bt.s = cur.s;
-        bt.b0 = cur.lo;
-        bt.end = cur.lo + cur.n;
-        bt.n = (int)min((long long)kBatch, bt.end - bt.b0);
-        return bt;
-    }
-
-    __device__ Batch advance(const Batch &b)
-    {
-        if (b.n == 0)
-            return b;
-        Batch nb = b;
-        nb.b0 = b.b0 + kBatch;
-        if (nb.b0 >= b.end)
-            return claim();
-        nb.n = (int)min((long long)kBatch, b.end - nb.b0);
-        return nb;
-    }
-};
-
-struct Coords3 {
-    double u, v, w;
-};
-
-__device__ __forceinline__ Coords3 load_uvw(const double *__restrict__ uvw, const Batch &b, int lane)
-{
-    Coords3 c{0.0, 0.0, 0.0};
-    if (lane < b.n) {
-        const double *p = uvw + 3 * (b.b0 + lane);
-        c.u = __ldg(p);
-        c.v = __ldg(p + 1);
-        c.w = __ldg(p + 2);
-    }
-    return c;
-}
-
-// Stage 2 of a batch: coordinates, keys, w rows and the copies of the g_u /
-// g_v rows (2 lanes per 32-byte row).
-__device__ __forceinline__ void issue_batch(const Batch &b, const Coords3 &c, const Geometry &g,
-                                            Stage &S, const float *__restrict__ guv,
-                                            const float *__restrict__ gwt, const float4 *wtab,
-                                            int lane, DeviceStatus *status)
-{
-    const bool in = lane < b.n;
-    VisCoords vc;
-    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
-    const int key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
-    const int fu = valid ? vc.fu : 0, fv = valid ? vc.fv : 0, fw = valid ? vc.fw : 0;
-    S.key[lane] = key;
-    S.fw[lane] = fw;
-    const int key0 = __shfl_sync(kFull, key, 0), fw0 = __shfl_sync(kFull, fw, 0);
-    const bool uniform = __all_sync(kFull, key == key0 && fw == fw0) && key0 >= 0;
-    if (lane == 0)
-        S.uniform = uniform;
-    const unsigned bad = __ballot_sync(kFull, in && !valid);
-    if (lane == 0 && bad)
-        atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));
-    if (wtab)
-        reinterpret_cast<float4 *>(S.gw)[lane] = wtab[fw];
-    else
-        cp_async16(smem_u32(S.gw[lane]), gwt + (size_t)fw * kWRow);
-    const int half = lane & 1;
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const int r = (lane >> 1) + 16 * m;
-        const int xu = __shfl_sync(kFull, fu, r);
-        const int xv = __shfl_sync(kFull, fv, r);
-        cp_async16(smem_u32(&S.gu[r][4 * half]), guv + (size_t)xu * kUVRow + 4 * half);
-        cp_async16(smem_u32(&S.gv[r][4 * half]), guv + (size_t)xv * kUVRow + 4 * half);
-    }
-    cp_async_commit();
-}
-
 template <int DT>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_DEGRID_MIN_BLOCKS)
 degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *__restrict__ scale,
@@ -273,17 +116,8 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // [w table (optional)] [one WarpSmem per warp]
-    const int wtab_bytes = g.w_table_rows > 0 ? ((g.w_table_rows * kWRow * 4 + 127) & ~127) : 0;
-    WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_raw + wtab_bytes)[threadIdx.x >> 5];
-    const float4 *wtab = nullptr;
-    if (wtab_bytes) {
-        float4 *t = reinterpret_cast<float4 *>(smem_raw);
-        const float4 *src = reinterpret_cast<const float4 *>(gwt);
-        for (int i = threadIdx.x; i < g.w_table_rows; i += blockDim.x)
-            t[i] = __ldg(src + i);
-        __syncthreads();
-        wtab = t;
-    }
+    WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_raw + wtable_bytes(g))[threadIdx.x >> 5];
+    const float4 *wtab = load_wtable(g, gwt, smem_raw);
     const int lane = threadIdx.x & 31;
     const int quarter = lane >> 3, q = lane & 7;
 
@@ -364,10 +198,7 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
 
 size_t smem_bytes(const degrid_plan *p, int warps)
 {
-    const size_t wt = p->geo.w_table_rows > 0
-                          ? ((size_t)p->geo.w_table_rows * kWRow * 4 + 127) & ~(size_t)127
-                          : 0;
-    return wt + sizeof(WarpSmem) * (size_t)warps;
+    return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)warps;
 }
 
 template <int DT>

@@ -1,0 +1,111 @@
+"""Autotuner for the persistent degridding kernel.
+
+The paper picks N_b, the visibilities per thread block, by hand and finds
+that the best value depends on the step du, dv, dw while N_b = 32 is good
+enough (Section "Results").  Here the equivalent knobs are the chunk size
+(visibilities per work item), warps per CTA and resident CTAs per SM; this
+module times a small grid of candidates on the caller's own inputs with CUDA
+events and keeps the fastest on the plan.  Results are cached in a JSON file
+keyed by GPU name, storage type and a coarse description of the inputs, so a
+later call with similar inputs reuses them without timing.
+
+The cache file is ``$DEGRID_TUNE_CACHE`` if set, else
+``~/.cache/gb300_degrid/tune.json``; ``DEGRID_TUNE=0`` disables timing (the
+cache is still read).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from typing import Iterable, Optional
+
+DEFAULT_CANDIDATES = [
+    (chunk, warps, bps)
+    for chunk in (128, 256, 512, 1024, 2048)
+    for warps in (4, 8)
+    for bps in (0,)
+]
+
+
+def _cache_path() -> str:
+    return os.environ.get("DEGRID_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "gb300_degrid", "tune.json"))
+
+
+def _load_cache() -> dict:
+    try:
+        with open(_cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store_cache(cache: dict) -> None:
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def cache_key(plan, n_subgrids: int, n_vis: int) -> str:
+    """GPU, storage type, subgrid shape and the orders of magnitude of S and N."""
+    import torch
+    name = torch.cuda.get_device_name(plan.device)
+    ny, nx, nz = plan.shape
+    return "%s|%s|%dx%dx%d|S~2^%d|N~2^%d" % (
+        name, plan.dtype, ny, nx, nz, int(math.log2(max(n_subgrids, 1))),
+        int(math.log2(max(n_vis, 1))))
+
+
+def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
+             candidates: Optional[Iterable] = None, iters: int = 5, use_cache: bool = True):
+    """Time `candidates` (chunk, warps_per_block, blocks_per_sm) and keep the best.
+
+    Returns {"tuning": {...}, "ms": best median kernel ms, "timings": [...]}.
+    """
+    import torch
+    S = int(vis_offsets.shape[0]) - 1
+    n = int(uvw.shape[0])
+    key = cache_key(plan, S, n)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        t = cache[key]["tuning"]
+        plan.set_tuning(t["chunk"], t["warps_per_block"], t["blocks_per_sm"])
+        return dict(cache[key], cached=True)
+    if os.environ.get("DEGRID_TUNE", "1") == "0":
+        return {"tuning": plan.tuning(), "ms": None, "timings": [], "cached": False}
+    cands = list(candidates) if candidates is not None else list(DEFAULT_CANDIDATES)
+    out = torch.empty(n, dtype=torch.complex64, device=plan.device)
+    plan.enable_timing(max(iters, 1))
+    timings = []
+    try:
+        for chunk, warps, bps in cands:
+            try:
+                plan.set_tuning(chunk, warps, bps)
+            except Exception:
+                continue
+            for _ in range(2):                      # warm-up (also sizes scratch)
+                plan.degrid(subgrids, uvw, vis_offsets, scale=scale, out=out)
+            for _ in range(iters):
+                plan.degrid(subgrids, uvw, vis_offsets, scale=scale, out=out)
+            ms = sorted(plan.kernel_times_ms(iters))
+            timings.append({"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
+                            "ms": ms[len(ms) // 2]})
+    finally:
+        plan.enable_timing(0)
+    if not timings:
+        raise RuntimeError("autotune: no candidate could be timed")
+    best = min(timings, key=lambda t: t["ms"])
+    plan.set_tuning(best["chunk"], best["warps_per_block"], best["blocks_per_sm"])
+    result = {"tuning": {k: best[k] for k in ("chunk", "warps_per_block", "blocks_per_sm")},
+              "ms": best["ms"], "timings": timings}
+    if use_cache:
+        cache[key] = {"tuning": result["tuning"], "ms": result["ms"]}
+        _store_cache(cache)
+    return dict(result, cached=False)

@@ -366,3 +366,37 @@ def test_cuda_graph_replay_is_identical(plan):
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(out.view(torch.float32), ref.view(torch.float32))
+
+
+def test_autotune_picks_a_candidate_and_caches_it(plan, tmp_path, monkeypatch):
+    monkeypatch.setenv("DEGRID_TUNE_CACHE", str(tmp_path / "tune.json"))
+    w = small_workload([6000, 3000], kind="line", seed=17)
+    sub, uvw, offs = upload(w, synth.subgrid_stack(2))
+    saved = plan.tuning()
+    try:
+        cands = [(128, 4, 0), (256, 8, 0), (512, 8, 1)]
+        res = dg.autotune(plan, sub, uvw, offs, candidates=cands, iters=2)
+        assert not res["cached"] and len(res["timings"]) == 3
+        assert plan.tuning() == res["tuning"]
+        again = dg.autotune(plan, sub, uvw, offs, candidates=cands, iters=2)
+        assert again["cached"] and again["tuning"] == res["tuning"]
+        ref, _ = oracle.degrid(G_UV, G_W, synth.subgrid_stack(2).astype(np.complex128), w.uvw,
+                               w.vis_offsets)
+        assert rel_l2(plan.degrid(sub, uvw, offs).cpu().numpy(), ref) <= TOL["c64"]
+    finally:
+        plan.set_tuning(saved["chunk"], saved["warps_per_block"], saved["blocks_per_sm"])
+
+
+def test_adjoint_dense_lines_full_size_sampled(plan):
+    # the gridding workload at full size: 32 subgrids x 100,000 visibilities;
+    # checked on 3 subgrids against the oracle's gridding of the same lists
+    d = dev()
+    w = synth.workload("diff32_100k")
+    y = synth.adjoint_vis(w.n_vis)
+    g = plan.grid(torch.from_numpy(y).to(d), torch.from_numpy(w.uvw).to(d),
+                  torch.from_numpy(w.vis_offsets).to(d), w.n_subgrids)
+    assert plan.status() == 0
+    for s in (0, 13, 31):
+        lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
+        ref, _ = oracle.grid(G_UV, G_W, SHAPE, 1, w.uvw[lo:hi], [0, hi - lo], y[lo:hi])
+        assert rel_l2(g[s].cpu().numpy(), ref[0]) <= TOL["c64"]
