@@ -223,6 +223,7 @@ class Workload:
     shape: tuple
     uvw: np.ndarray          # float64 [N][3]
     vis_offsets: np.ndarray  # int64 [S + 1]
+    ids: Optional[np.ndarray] = None   # global subgrid ids (a shard of a larger job)
 
     @property
     def n_vis(self) -> int:
@@ -232,23 +233,34 @@ class Workload:
         return np.diff(self.vis_offsets)
 
     def subgrid(self, s: int) -> np.ndarray:
-        return subgrid(s, self.shape)
+        return subgrid(int(self.ids[s]) if self.ids is not None else s, self.shape)
 
     def subgrids(self) -> np.ndarray:
-        return subgrid_stack(self.n_subgrids, self.shape)
+        if self.ids is None:
+            return subgrid_stack(self.n_subgrids, self.shape)
+        out = np.empty((self.n_subgrids,) + tuple(self.shape), dtype=np.complex64)
+        for s in range(self.n_subgrids):
+            out[s] = self.subgrid(s)
+        return out
 
     def subgrid_nbytes(self, elem_bytes: int = 8) -> int:
         ny, nx, nz = self.shape
         return self.n_subgrids * ny * nx * nz * elem_bytes
 
 
-def lines_workload(name: str, counts, shape=SUBGRID_SHAPE) -> Workload:
-    """Every subgrid's list is its own random line (the paper's test case)."""
+def lines_workload(name: str, counts, shape=SUBGRID_SHAPE, ids=None) -> Workload:
+    """Every subgrid's list is its own random line (the paper's test case).
+
+    With `ids`, the subgrids are those global ids of a larger job (their
+    values and lists are the ones that job would have).
+    """
     counts = [int(c) for c in counts]
-    parts = [random_line(c, np.random.default_rng([SEED_UVW, s]), shape)
-             for s, c in enumerate(counts)]
+    gid = list(range(len(counts))) if ids is None else [int(i) for i in ids]
+    parts = [random_line(c, np.random.default_rng([SEED_UVW, g]), shape)
+             for g, c in zip(gid, counts)]
     uvw = np.ascontiguousarray(np.concatenate(parts, axis=0)) if parts else np.zeros((0, 3))
-    return Workload(name, len(counts), tuple(shape), uvw, offsets_from_counts(counts))
+    return Workload(name, len(counts), tuple(shape), uvw, offsets_from_counts(counts),
+                    None if ids is None else np.asarray(gid, dtype=np.int64))
 
 
 def batched_counts(n_subgrids: int, lo: float = 1e3, hi: float = 1e6) -> np.ndarray:
