@@ -40,6 +40,15 @@ WORKLOAD_DESC = ("64 subgrids of 512x512x4 complex64 (i.i.d. complex Gaussian), 
                  "separable Kaiser-Bessel G_uv support 8 oversampling 16384, G_w support 4 "
                  "oversampling 128")
 FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 4 flop)
+# DRAM bytes (read + write) per visibility of degrid_kernel<DG_C64>, from one ncu capture
+# (profiles/degrid_kernel_lines16_250k_ncu.md: 4,000,000 visibilities; the traffic is uvw,
+# output and footprints, all proportional to the visibilities).  Valid only for the kernel
+# sources it was taken on: the bench reports null traffic once they change.
+TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
+                          "paper_2102_12739_gb300/csrc/pipeline.cuh",
+                          "paper_2102_12739_gb300/csrc/internal.cuh")
+TRAFFIC_SHA = "a541833dfeab6980"
+TRAFFIC_BYTES_PER_VIS = (103.251200e6 + 12.664576e6) / 4_000_000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
@@ -317,6 +326,25 @@ def adjoint_section(torch, dg, synth, dev, flush, steps):
             "steps": steps}
 
 
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_vis):
+    """DRAM bytes per launch from the ncu capture, or None if the kernel changed since."""
+    try:
+        if kernel_sources_sha() != TRAFFIC_SHA:
+            return None
+    except OSError:
+        return None
+    return TRAFFIC_BYTES_PER_VIS * n_vis
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2102_12739_gb300 as dg
@@ -395,7 +423,7 @@ def run_ours(args, rank, world):
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = w.n_vis * FLOP_PER_VIS / (mean_kern * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": measured_traffic(w.n_vis),
                 "kernel": "degrid_kernel<DG_C64>",
                 "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
@@ -422,21 +450,38 @@ def run_ours(args, rank, world):
     }
 
     if not args.no_sweep:
-        sweep = {"c64": {"value": value, "kernel_ms": mean_kern, "rel_l2": err_c64[0]}}
-        for dt in ("f16", "bf16"):
-            codes, scale = dg.pack_subgrids(sub, dt)
-            with dg.DegridPlan(dtype=dt, device=dev) as p2:
-                p2.enable_timing(args.sweep_steps)
-                o2 = torch.empty_like(out)
+        # config 3: each storage type, plain and with the compensated reduction; errors
+        # against the FP64 oracle on the original complex64 subgrids (quantisation
+        # included) and, for FP16/BF16, on the values the kernel reads (kernel error)
+        sweep = {"c64": {"value": value, "kernel_ms": mean_kern, "rel_l2": err_c64[0],
+                         "max_abs": err_c64[1], "compensated": False}}
+        for dt in ("c64", "f16", "bf16"):
+            if dt == "c64":
+                codes, scale, stored_np = sub, None, None
+            else:
+                codes, scale = dg.pack_subgrids(sub, dt)
+                import oracle
+                picked = np.linspace(0, w.n_subgrids - 1, 4).astype(int)
+                qc, qs = oracle.quantize(sub_np[picked], dt)
+                deq = oracle.dequantize(qc, qs, dt)         # exact, complex128
+                stored_np = {int(s_): deq[k] for k, s_ in enumerate(picked)}
+            for comp in ((True,) if dt == "c64" else (False, True)):
+                with dg.DegridPlan(dtype=dt, device=dev, compensated=comp) as p2:
+                    p2.enable_timing(args.sweep_steps)
+                    o2 = torch.empty_like(out)
 
-                def step2():
-                    p2.degrid(codes, uvw, offs, scale=scale, out=o2)
-                warm_up(torch, step2, flush, args.warmup, min_seconds=0.3)
-                s_ms, k_ms = time_steps(torch, p2, step2, args.sweep_steps, flush, stream)
-                e = sampled_error(o2.cpu().numpy(), w, g_uv, g_w, sub_np)
-            ms = sum(s_ms) / len(s_ms)
-            sweep[dt] = {"value": w.n_vis / (ms * 1e-3), "kernel_ms": sum(k_ms) / len(k_ms),
-                         "rel_l2": e[0], "max_abs": e[1]}
+                    def step2():
+                        p2.degrid(codes, uvw, offs, scale=scale, out=o2)
+                    warm_up(torch, step2, flush, args.warmup, min_seconds=0.3)
+                    s_ms, k_ms = time_steps(torch, p2, step2, args.sweep_steps, flush, stream)
+                    o2_np = o2.cpu().numpy()
+                    e = sampled_error(o2_np, w, g_uv, g_w, sub_np)
+                    ek = sampled_error(o2_np, w, g_uv, g_w, stored_np) if stored_np is not None else e
+                ms = sum(s_ms) / len(s_ms)
+                sweep[dt + ("_compensated" if comp else "")] = {
+                    "value": w.n_vis / (ms * 1e-3), "kernel_ms": sum(k_ms) / len(k_ms),
+                    "rel_l2": e[0], "max_abs": e[1], "rel_l2_vs_stored_values": ek[0],
+                    "compensated": comp}
             del codes, scale
         line["precision_sweep"] = sweep
 

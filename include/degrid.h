@@ -81,7 +81,8 @@ const char *degrid_version(void);
  * and the 512 x 512 x 4 subgrid shape are the fixed inputs of the method).
  *   out            receives the plan handle (set to NULL on failure)
  *   nx, ny, nz     subgrid extent; layout [S][ny][nx][nz]; nz >= w_support,
- *                  ny * nx * nz < 2^31
+ *                  ny * nx * nz < 2^31, max(nx, ny) * uv_oversample <= 2^31
+ *                  and nz * w_oversample <= 2^31 (else DG_ERR_UNSUPPORTED)
  *   g_uv           HOST double [uv_oversample][uv_support], copied (and
  *                  rounded to FP32) to the device; the caller keeps it
  *   uv_support     must be 8 (the paper's 8 x 8 footprint)
@@ -117,6 +118,20 @@ void degrid_plan_destroy(degrid_plan_t plan);
  */
 dg_status degrid_plan_set_tuning(degrid_plan_t plan, int chunk, int warps_per_block,
                                  int blocks_per_sm);
+
+/*
+ * Compensated reduction (the precision pattern of the target: FP32
+ * accumulation with compensated summation of the partial sums that lanes
+ * exchange).  With enabled = 1, every addition of the cross-lane reduction of
+ * degrid_execute is an error-free TwoSum (Knuth) and the rounding errors are
+ * added back at the end, so the combination of the four lane partials of a
+ * visibility is exact before one final rounding; the per-lane FMA chains are
+ * unchanged.  enabled = 0 (the default) adds the partials plainly.  Both
+ * forms are deterministic.  Returns DG_OK, or DG_ERR_ARG for a NULL plan or
+ * a value other than 0 / 1.  Not used by grid_adjoint_execute.
+ */
+dg_status degrid_plan_set_compensated(degrid_plan_t plan, int enabled);
+dg_status degrid_plan_get_compensated(degrid_plan_t plan, int *enabled);
 
 /* Read back the current tuning (any pointer may be NULL). */
 dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_block,
@@ -225,7 +240,8 @@ dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid
  * It computes the same visibilities as degrid_execute, but takes no plan:
  *   g_uv, g_w      DEVICE float tables [uv_oversample][8] and [w_oversample][4]
  *                  (the FP32 values degrid_plan_create would store)
- *   nx, ny, nz,    as for degrid_plan_create (supports 8 and 4 implied)
+ *   nx, ny, nz,    as for degrid_plan_create (supports 8 and 4 implied;
+ *                  a shape outside its limits gives DG_ERR_ARG here)
  *   uv_oversample, w_oversample, dtype
  *   status_out     DEVICE unsigned long long [2] or NULL: receives the number
  *                  of invalid visibilities and error flags (bit 0: malformed

@@ -74,7 +74,7 @@ class DegridPlan:
     """
 
     def __init__(self, shape=synth.SUBGRID_SHAPE, g_uv=None, g_w=None, dtype: str = "c64",
-                 device=None):
+                 device=None, compensated: bool = False):
         torch = _torch()
         lib = load()
         if dtype not in DTYPES:
@@ -104,6 +104,8 @@ class DegridPlan:
                                     device.index)
         check(st, "degrid_plan_create")
         self._h = h
+        if compensated:
+            self.set_compensated(True)
 
     # -- lifetime --------------------------------------------------------
     @property
@@ -139,6 +141,18 @@ class DegridPlan:
         check(load().degrid_plan_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(w),
                                             ctypes.byref(b)), "degrid_plan_get_tuning")
         return {"chunk": c.value, "warps_per_block": w.value, "blocks_per_sm": b.value}
+
+    def set_compensated(self, enabled: bool = True) -> None:
+        """Compensated (TwoSum) reduction of the lane partials in degrid()."""
+        check(load().degrid_plan_set_compensated(self.handle, 1 if enabled else 0),
+              "degrid_plan_set_compensated")
+
+    @property
+    def compensated(self) -> bool:
+        v = ctypes.c_int()
+        check(load().degrid_plan_get_compensated(self.handle, ctypes.byref(v)),
+              "degrid_plan_get_compensated")
+        return bool(v.value)
 
     def enable_timing(self, n_slots: int = 4096) -> None:
         """Record a CUDA event pair around the main kernel of each of the next

@@ -37,6 +37,8 @@ SIGNATURES = {
     "degrid_plan_destroy": (None, [_P]),
     "degrid_plan_set_tuning": (_I, [_P, _I, _I, _I]),
     "degrid_plan_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "degrid_plan_set_compensated": (_I, [_P, _I]),
+    "degrid_plan_get_compensated": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_enable_timing": (_I, [_P, _I]),
     "degrid_plan_kernel_times_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I,
                                          ctypes.POINTER(_I)]),

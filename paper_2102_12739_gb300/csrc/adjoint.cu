@@ -93,7 +93,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
     const int lane = threadIdx.x & 31;
     const int quarter = lane >> 3, q = lane & 7;
 
-    Claimer claimer(sched, lane);
+    Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), vis_in, (int)sizeof(float2)});
     Batch bB = claimer.claim();
     if (bB.n == 0)
         return;

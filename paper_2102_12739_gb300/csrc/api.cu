@@ -197,6 +197,9 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     const int l2uv = log2_exact(uv_oversample), l2w = log2_exact(w_oversample);
     if (l2uv < 0 || l2w < 0 || l2uv > 20 || l2w > 20)
         return DG_ERR_ARG;
+    // every valid oversampled coordinate p = rint(q * O) < n * O must fit 31 bits
+    if (((int64_t)(nx > ny ? nx : ny) << l2uv) > ((int64_t)1 << 31) || ((int64_t)nz << l2w) > ((int64_t)1 << 31))
+        return DG_ERR_UNSUPPORTED;
 
     int n_dev = 0;
     if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device >= n_dev)
@@ -297,6 +300,25 @@ dg_status degrid_plan_set_tuning(degrid_plan_t p, int chunk, int warps_per_block
     }
     if (blocks_per_sm >= 0)
         p->blocks_per_sm = blocks_per_sm;
+    return DG_OK;
+}
+
+dg_status degrid_plan_set_compensated(degrid_plan_t p, int enabled)
+{
+    if (!p || (enabled != 0 && enabled != 1))
+        return DG_ERR_ARG;
+    if (enabled != p->compensated) {
+        p->compensated = enabled;
+        p->max_blocks_degrid = 0;               // another kernel instance
+    }
+    return DG_OK;
+}
+
+dg_status degrid_plan_get_compensated(degrid_plan_t p, int *enabled)
+{
+    if (!p || !enabled)
+        return DG_ERR_ARG;
+    *enabled = p->compensated;
     return DG_OK;
 }
 

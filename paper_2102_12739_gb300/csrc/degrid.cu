@@ -5,8 +5,8 @@
 // of consecutive visibilities of one subgrid in batches of 32.  Per batch
 // three stages overlap across consecutive batches of a warp:
 //  1. the FP64 coordinates of batch n + 2 are loaded into registers;
-//  2. batch n + 1 is snapped and its GCF rows are copied into the warp's
-//     shared-memory stage with cp.async;
+//  2. batch n + 1 is snapped (one visibility per lane) and its g_u and g_v
+//     rows are copied into the warp's shared-memory stage with cp.async;
 //  3. batch n is summed from the stage that arrived.
 //
 // Footprint sum.  The separable weights let the 8 x 8 x 4 sum be taken in
@@ -15,21 +15,26 @@
 // and M depends only on the footprint start and the w-kernel row.  On a dense
 // list hundreds of consecutive visibilities share both (the reuse the paper
 // notes for D1), so M is computed once per run and each visibility then costs
-// 72 complex x real products instead of 256.  Each quarter-warp computes one
-// visibility (4 per step, 8 steps per batch); lane q of a quarter keeps the
-// column M[0..7][q] in registers, accumulates along v (b) as D1 does, and
-// scales by g_u[q].  A batch whose 32 visibilities share one footprint and
-// one w row takes a branch-free path; otherwise each quarter checks, and
-// rebuilds its M when its visibility needs another one (so every input is
-// handled, at up to 82 products per visibility when nothing is shared).
+// 72 complex x real products instead of 256.
+//
+// Lanes.  Four lanes share a visibility: lane 8j + p (j = 0..3, p = 0..7)
+// holds the rows M[2j][0..7] and M[2j+1][0..7] of the footprint in 32
+// registers and, for a visibility r, forms
+// sum_{b = 2j, 2j+1} g_v[b] sum_a g_u[a] M[b][a] (36 FP32 operations).  A
+// batch takes four passes; in pass k lane 8j + p works on visibility
+// 8 (k ^ j) + p, an order chosen so that the two exchange steps of the
+// reduction move the same pass slots on every lane (no selects): lane xor 16
+// adds slots 2, 3 to 0, 1, then lane xor 8 adds slot 1 to slot 0, and lane
+// 8j + p ends with visibility 8j + p, so the warp writes its 32 results into
+// one contiguous 256-byte segment in lane order.  The 8 lanes of one 128-bit
+// shared-memory wavefront read 8 consecutive rows of the stage, which its
+// half-swapped layout places in 8 different bank groups.  M is built by the whole warp (two
+// entries per lane) into shared memory and read back by rows; a batch whose
+// 32 visibilities share one footprint and w row needs no checks, and any
+// other batch is summed once per distinct (footprint, w row) it holds, every
+// lane keeping the pass that matches its own visibility.
 // Scalar FP32 FMAs: packed FFMA2 with three distinct register pairs ran at
 // about half the FP32 peak on this part.
-//
-// Reduction and output.  The 8 partials of a quarter are reduced with a
-// transposing butterfly (3 shuffle levels that halve the live values), after
-// which every lane holds one whole visibility; the warp writes its 32
-// results into one contiguous 256-byte segment (the paper's bulk contiguous
-// write-out, without the shared-memory staging).
 #include "pipeline.cuh"
 
 namespace dg {
@@ -41,73 +46,75 @@ namespace {
 
 constexpr int kMaxWarps = 8;                // per CTA
 struct alignas(128) WarpSmem {
-    Stage st[2];
-    float2 part[8][kWarp];      // per-step partials on the mixed path
+    RowStage st[2];
+    float2 m[8][8];             // M[b][a] of the footprint being built
+    float2 part[4][kWarp];      // per-pass partials on the mixed path
 };
 
 // ---- the factored sum -------------------------------------------------------
 
-// M[b] = sum_c g_w[c] s[y0 + b][x0 + q][z0 + c] for b = 0..7 (this lane's
-// column q of the footprint with origin `key` in the subgrid at `base`).
+// M[2j + i][a] for i = 0, 1 and a = 0..7 of footprint `key` (subgrid at
+// `base`) with w row gw: lane (a = lane & 7, b = lane >> 3 and b + 4)
+// computes two entries into shared memory, then every lane reads its rows.
 template <int DT>
-__device__ __forceinline__ void build_column(float2 (&M)[8], const void *sub, int64_t base, int key,
-                                             int q, const float4 &gw, const Geometry &g)
+__device__ __forceinline__ void build_rows(float2 (&M)[2][8], float2 (&mbuf)[8][8], const void *sub,
+                                           int64_t base, int key, const float4 &gw, const Geometry &g,
+                                           int lane, int j)
 {
-    const int64_t col = base + key + (int64_t)q * g.nz;
+    const int a = lane & 7, b = lane >> 3;
+    const int64_t col = base + key + (int64_t)a * g.nz;
+    __syncwarp();                               // previous read-back done
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const int64_t e = col + (int64_t)b * g.row_stride;
+    for (int k = 0; k < 2; ++k) {
+        const int64_t e = col + (int64_t)(b + 4 * k) * g.row_stride;
         const float2 s0 = Storage<DT>::load(sub, e), s1 = Storage<DT>::load(sub, e + 1);
         const float2 s2 = Storage<DT>::load(sub, e + 2), s3 = Storage<DT>::load(sub, e + 3);
-        M[b].x = fmaf(s3.x, gw.w, fmaf(s2.x, gw.z, fmaf(s1.x, gw.y, s0.x * gw.x)));
-        M[b].y = fmaf(s3.y, gw.w, fmaf(s2.y, gw.z, fmaf(s1.y, gw.y, s0.y * gw.x)));
+        float2 m;
+        m.x = fmaf(s3.x, gw.w, fmaf(s2.x, gw.z, fmaf(s1.x, gw.y, s0.x * gw.x)));
+        m.y = fmaf(s3.y, gw.w, fmaf(s2.y, gw.z, fmaf(s1.y, gw.y, s0.y * gw.x)));
+        mbuf[b + 4 * k][a] = m;
     }
-}
-
-// This lane's part of visibility r: g_u[q] * sum_b g_v[b] M[b] (18 FP32 ops).
-__device__ __forceinline__ float2 apply_column(const float2 (&M)[8], const Stage &S, int r, int q)
-{
-    const float4 v0 = reinterpret_cast<const float4 *>(S.gv[r])[0];
-    const float4 v1 = reinterpret_cast<const float4 *>(S.gv[r])[1];
-    const float gu = S.gu[r][q];
-    float re = M[0].x * v0.x, im = M[0].y * v0.x;
-    re = fmaf(M[1].x, v0.y, re);
-    im = fmaf(M[1].y, v0.y, im);
-    re = fmaf(M[2].x, v0.z, re);
-    im = fmaf(M[2].y, v0.z, im);
-    re = fmaf(M[3].x, v0.w, re);
-    im = fmaf(M[3].y, v0.w, im);
-    re = fmaf(M[4].x, v1.x, re);
-    im = fmaf(M[4].y, v1.x, im);
-    re = fmaf(M[5].x, v1.y, re);
-    im = fmaf(M[5].y, v1.y, im);
-    re = fmaf(M[6].x, v1.z, re);
-    im = fmaf(M[6].y, v1.z, im);
-    re = fmaf(M[7].x, v1.w, re);
-    im = fmaf(M[7].y, v1.w, im);
-    return make_float2(re * gu, im * gu);
-}
-
-// Transposing butterfly over the 8 lanes of a quarter: on entry P[t] is this
-// lane's partial of step t; on exit the lane returns the total of step q.
-__device__ __forceinline__ float2 quarter_reduce(float2 (&P)[8], int q)
-{
+    __syncwarp();
 #pragma unroll
-    for (int h = 4; h >= 1; h >>= 1) {
-        const bool up = (q & h) != 0;
+    for (int i = 0; i < 2; ++i) {
 #pragma unroll
-        for (int j = 0; j < h; ++j) {
-            float2 send = up ? P[j] : P[j + h];
-            const float2 keep = up ? P[j + h] : P[j];
-            send.x = __shfl_xor_sync(kFull, send.x, h);
-            send.y = __shfl_xor_sync(kFull, send.y, h);
-            P[j] = __fadd2_rn(keep, send);
+        for (int a2 = 0; a2 < 8; a2 += 2) {
+            const float4 t = *reinterpret_cast<const float4 *>(&mbuf[2 * j + i][a2]);
+            M[i][a2] = make_float2(t.x, t.y);
+            M[i][a2 + 1] = make_float2(t.z, t.w);
         }
     }
-    return P[0];
 }
 
-template <int DT>
+// This lane's quarter of visibility r: sum_{i} g_v[2j + i] sum_a g_u[a] M[i][a].
+__device__ __forceinline__ float2 quarter_sum(const float2 (&M)[2][8], const RowStage &S, int r, int j)
+{
+    const float4 u0 = S.u[r][row_half(r, 0)];
+    const float4 u1 = S.u[r][row_half(r, 1)];
+    const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
+    const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    float2 t0 = make_float2(M[0][0].x * gu[0], M[0][0].y * gu[0]);
+    float2 t1 = make_float2(M[1][0].x * gu[0], M[1][0].y * gu[0]);
+#pragma unroll
+    for (int a = 1; a < 8; ++a) {
+        t0.x = fmaf(M[0][a].x, gu[a], t0.x);
+        t0.y = fmaf(M[0][a].y, gu[a], t0.y);
+        t1.x = fmaf(M[1][a].x, gu[a], t1.x);
+        t1.y = fmaf(M[1][a].y, gu[a], t1.y);
+    }
+    return make_float2(fmaf(t1.x, v.y, t0.x * v.x), fmaf(t1.y, v.y, t0.y * v.x));
+}
+
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+template <int DT, bool COMP>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_DEGRID_MIN_BLOCKS)
 degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *__restrict__ scale,
               const double *__restrict__ uvw, const float *__restrict__ guv,
@@ -119,29 +126,34 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_raw + wtable_bytes(g))[threadIdx.x >> 5];
     const float4 *wtab = load_wtable(g, gwt, smem_raw);
     const int lane = threadIdx.x & 31;
-    const int quarter = lane >> 3, q = lane & 7;
+    const int p = lane & 7, j = lane >> 3;
 
-    Claimer claimer(sched, lane);
+    Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), nullptr, 0});
     Batch bB = claimer.claim();         // rows in flight
     if (bB.n == 0)
         return;
-    issue_batch(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, gwt, wtab, lane, status);
+    Issued iB = issue_rows(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
     Batch bC = claimer.advance(bB);     // coordinates in registers
     Coords3 cC = load_uvw(uvw, bC, lane);
 
     int stage = 0;
-    float2 M[8];                        // footprint column M[0..7][q] of (m_key, m_fw, m_s)
+    float2 M[2][8];                     // rows 2j, 2j + 1 of M for (m_key, m_fw) in subgrid m_s
     int m_key = -2, m_fw = -1, m_s = -1;
+    int64_t base = 0;
+    float sc = 1.f;
 #pragma unroll
-    for (int b = 0; b < 8; ++b)
-        M[b] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            M[i][a] = make_float2(0.f, 0.f);
 
     while (bB.n > 0) {
         const Batch bA = bB;            // summed in this iteration
+        const Issued iA = iB;
         const int sA = stage;
         bB = bC;
         if (bB.n > 0)
-            issue_batch(bB, cC, g, ws.st[sA ^ 1], guv, gwt, wtab, lane, status);
+            iB = issue_rows(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
         bC = claimer.advance(bC);
         cC = load_uvw(uvw, bC, lane);
         if (bB.n > 0)
@@ -150,47 +162,95 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
             cp_async_wait<0>();
         __syncwarp();
 
-        const Stage &S = ws.st[sA];
+        const RowStage &S = ws.st[sA];
         if (bA.s != m_s) {
             m_s = bA.s;
             m_key = -2;
+            base = (int64_t)bA.s * g.plane;
+            if (DT != DG_C64)
+                sc = __ldg(scale + bA.s);
         }
-        const int64_t base = (int64_t)bA.s * g.plane;
-        float2 P[8];
-        if (S.uniform) {
-            const int k0 = S.key[0], f0 = S.fw[0];
-            if (k0 != m_key || f0 != m_fw) {
-                build_column<DT>(M, subgrids, base, k0, q, reinterpret_cast<const float4 *>(S.gw)[0], g);
-                m_key = k0;
-                m_fw = f0;
+        float2 P[4];                    // pass k: this lane's quarter of visibility 8 (k ^ j) + p
+        if (iA.uniform) {
+            if (iA.key0 != m_key || iA.fw0 != m_fw) {
+                const float4 gw = wtab ? wtab[iA.fw0] : __ldg(reinterpret_cast<const float4 *>(gwt) + iA.fw0);
+                build_rows<DT>(M, ws.m, subgrids, base, iA.key0, gw, g, lane, j);
+                m_key = iA.key0;
+                m_fw = iA.fw0;
             }
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                P[t] = apply_column(M, S, 4 * t + quarter, q);
+            for (int k = 0; k < 4; ++k)
+                P[k] = quarter_sum(M, S, 8 * (k ^ j) + p, j);
         } else {
+            // Pass k covers visibilities 8k .. 8k + 7 here, so a change of
+            // footprint inside a run of the list touches one pass.  Each pass
+            // is summed once per distinct (footprint, w row) among its
+            // visibilities, every lane keeping the sum that matches its own
+            // (invalid ones, key -1, stay zero); the partials then move to
+            // the slots of the permuted order, slot k = pass k ^ j.
 #pragma unroll 1
-            for (int t = 0; t < 8; ++t) {
-                const int r = 4 * t + quarter;
-                const int kv = S.key[r], fv = S.fw[r];
-                if (kv >= 0 && (kv != m_key || fv != m_fw)) {
-                    build_column<DT>(M, subgrids, base, kv, q, reinterpret_cast<const float4 *>(S.gw)[r], g);
-                    m_key = kv;
-                    m_fw = fv;
+            for (int k = 0; k < 4; ++k) {
+                const int r = 8 * k + p;
+                const int kr = __shfl_sync(kFull, iA.key, r);
+                const int fr = __shfl_sync(kFull, iA.fw, r);
+                bool done = kr < 0;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+                while (true) {
+                    const unsigned todo = __ballot_sync(kFull, !done);
+                    if (todo == 0)
+                        break;
+                    const int leader = __ffs(todo) - 1;
+                    const int lk = __shfl_sync(kFull, kr, leader);
+                    const int lf = __shfl_sync(kFull, fr, leader);
+                    if (lk != m_key || lf != m_fw) {
+                        const float4 gw = wtab ? wtab[lf] : __ldg(reinterpret_cast<const float4 *>(gwt) + lf);
+                        build_rows<DT>(M, ws.m, subgrids, base, lk, gw, g, lane, j);
+                        m_key = lk;
+                        m_fw = lf;
+                    }
+                    const float2 x = quarter_sum(M, S, r, j);
+                    const bool mine = !done && kr == lk && fr == lf;
+                    if (mine)
+                        acc = x;
+                    done = done || mine;
                 }
-                ws.part[t][lane] = kv >= 0 ? apply_column(M, S, r, q) : make_float2(0.f, 0.f);
+                ws.part[k][lane] = acc;
             }
+            __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                P[t] = ws.part[t][lane];
+            for (int k = 0; k < 4; ++k)
+                P[k] = ws.part[k ^ j][lane];
         }
-        float2 V = quarter_reduce(P, q);
-        const int r_out = 4 * q + quarter;
-        if (DT != DG_C64) {
-            const float sc = __ldg(scale + bA.s);
+        // lane xor 16 (j ^ 2) brings slots 2, 3 onto 0, 1; lane xor 8 (j ^ 1)
+        // brings slot 1 onto 0
+        float2 V;
+        if (COMP) {
+            // the same three additions as error-free sums; the four rounding
+            // errors are summed and added back once
+            float2 e0, e1, e;
+            P[0].x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[2].x, 16), e0.x);
+            P[0].y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[2].y, 16), e0.y);
+            P[1].x = two_sum(P[1].x, __shfl_xor_sync(kFull, P[3].x, 16), e1.x);
+            P[1].y = two_sum(P[1].y, __shfl_xor_sync(kFull, P[3].y, 16), e1.y);
+            V.x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[1].x, 8), e.x);
+            V.y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[1].y, 8), e.y);
+            e.x += e0.x + __shfl_xor_sync(kFull, e1.x, 8);
+            e.y += e0.y + __shfl_xor_sync(kFull, e1.y, 8);
+            V.x += e.x;
+            V.y += e.y;
+        } else {
+            P[0].x += __shfl_xor_sync(kFull, P[2].x, 16);
+            P[0].y += __shfl_xor_sync(kFull, P[2].y, 16);
+            P[1].x += __shfl_xor_sync(kFull, P[3].x, 16);
+            P[1].y += __shfl_xor_sync(kFull, P[3].y, 16);
+            V.x = P[0].x + __shfl_xor_sync(kFull, P[1].x, 8);
+            V.y = P[0].y + __shfl_xor_sync(kFull, P[1].y, 8);
+        }
+        if (DT != DG_C64)
             V = __fmul2_rn(V, make_float2(sc, sc));
-        }
-        if (r_out < bA.n)
-            vis_out[bA.b0 + r_out] = V;
+        if (lane < bA.n)                // lane 8j + p holds visibility 8j + p
+            vis_out[bA.b0 + lane] = V;
         __syncwarp();
         stage ^= 1;
     }
@@ -201,33 +261,47 @@ size_t smem_bytes(const degrid_plan *p, int warps)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)warps;
 }
 
-template <int DT>
+template <int DT, bool COMP>
 cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                    const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    degrid_kernel<DT><<<grid_blocks, threads, smem, st>>>(p->geo, subgrids, scale, uvw, p->guv,
-                                                           p->gw, sched, out, p->status);
+    degrid_kernel<DT, COMP><<<grid_blocks, threads, smem, st>>>(p->geo, subgrids, scale, uvw, p->guv,
+                                                                 p->gw, sched, out, p->status);
     return cudaGetLastError();
 }
 
-template <int DT>
+template <int DT, bool COMP>
 int max_blocks(degrid_plan *p)
 {
     int n = 0;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    if (cudaFuncSetAttribute(degrid_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP>,
                                                       p->warps_per_block * kWarp, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+template <int DT>
+cudaError_t launch_dt(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
+                      const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
+{
+    return p->compensated ? launch<DT, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
+                          : launch<DT, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+}
+
+template <int DT>
+int max_blocks_dt(degrid_plan *p)
+{
+    return p->compensated ? max_blocks<DT, true>(p) : max_blocks<DT, false>(p);
 }
 
 }  // namespace
@@ -243,11 +317,11 @@ cudaError_t dg_launch_degrid(degrid_plan *p, cudaStream_t st, const void *subgri
     float2 *out = reinterpret_cast<float2 *>(out_f);
     switch (p->dtype) {
     case DG_C64:
-        return launch<DG_C64>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+        return launch_dt<DG_C64>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
     case DG_C32_F16:
-        return launch<DG_C32_F16>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+        return launch_dt<DG_C32_F16>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
     case DG_C32_BF16:
-        return launch<DG_C32_BF16>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+        return launch_dt<DG_C32_BF16>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
     }
     return cudaErrorInvalidValue;
 }
@@ -256,9 +330,9 @@ int dg_max_blocks_per_sm_degrid(degrid_plan *p)
 {
     using namespace dg;
     switch (p->dtype) {
-    case DG_C64: return max_blocks<DG_C64>(p);
-    case DG_C32_F16: return max_blocks<DG_C32_F16>(p);
-    case DG_C32_BF16: return max_blocks<DG_C32_BF16>(p);
+    case DG_C64: return max_blocks_dt<DG_C64>(p);
+    case DG_C32_F16: return max_blocks_dt<DG_C32_F16>(p);
+    case DG_C32_BF16: return max_blocks_dt<DG_C32_BF16>(p);
     }
     return 1;
 }

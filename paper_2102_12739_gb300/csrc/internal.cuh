@@ -33,32 +33,44 @@ struct Geometry {
 //
 // Per axis with support W and oversampling O = 2^k: p = rint(q * O) with
 // ties to even, i = floor(p / O), f = p - i * O, start = i - W/2 + 1; valid
-// when 0 <= start <= n - W.  Computed exactly with integer operations on the
-// IEEE-754 pattern of q, without FP64 arithmetic (FP64 runs at 1/64 of the
-// FP32 rate on this part):
-//   * q <= 0 (including -0, negative NaN) gives p <= 0, i <= 0, start < 0;
-//   * with m the 53-bit significand and e the biased exponent,
-//     q * O = m * 2^-r, r = 1075 - k - e.  r > 53 means q * O < 0.5, so
-//     p = 0 and start < 0; r < 1 means q * O >= 2^52 (or q is inf / NaN),
-//     far beyond any subgrid (n * O < 2^52).  All these are invalid;
-//   * otherwise p = (m + 2^(r-1) - 1 + bit_r(m)) >> r, which is m / 2^r
-//     rounded to nearest with ties to the even neighbour.
+// when 0 <= start <= n - W.  Computed exactly with 32-bit integer operations
+// on the IEEE-754 pattern of q, without FP64 arithmetic (FP64 runs at a small
+// fraction of the FP32 rate on this part).  With hi:lo the two words of q,
+// e its biased exponent and m its 53-bit significand, q * O = m * 2^-(D)
+// with D = 1075 - k - e.  Left-aligning the significand, X = m << 11 (the
+// implicit bit lands in bit 63), the integer part of q * O is X >> (D + 11)
+// and the bits shifted out are the fraction.  For a valid coordinate
+// q * O < n * O <= 2^31, so D + 11 >= 32 and, with R = D + 11 - 32:
+//   I = Xh >> R                      integer part (Xh, Xl: words of X)
+//   F = low word of (X >> R)         the 32 fraction bits below I
+//   sticky = Xl mod 2^R != 0         any fraction bit below F
+// and rounding to nearest, ties to even, adds one exactly when
+// F | sticky | (I & 1) > 2^31 (the low bit stands in for "above half" when
+// sticky is set and for "odd" at an exact tie).  Shifts saturate at 32
+// (funnel shifts with clamping), so every out-of-range input lands on an
+// invalid start with no extra test:
+//   * q <= 0, denormal, or q * O < 1/2: R >= 32 (e small, or e < 0 through
+//     the arithmetic shift of a negative q), I = 0, p <= 1, start < 0;
+//   * q * O >= 2^32, inf, NaN: R < 0, a huge unsigned shift, I = 0 again.
+// W >= 4 makes every start from p <= 1 negative; the plan requires
+// n * O <= 2^31 so every valid p fits the 32-bit word.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool snap_axis(double q, int log2_os, int support, int n,
                                           int &start, int &frac)
 {
-    const long long bits = __double_as_longlong(q);
-    if (bits <= 0)
-        return false;
-    const int r = 1075 - log2_os - (int)(bits >> 52);
-    if (r < 1 || r > 53)
-        return false;
-    const unsigned long long m = ((unsigned long long)bits & 0x000fffffffffffffull) | 0x0010000000000000ull;
-    const unsigned long long p = (m + ((1ull << (r - 1)) - 1ull) + ((m >> r) & 1ull)) >> r;
-    frac = (int)(p & ((1ull << log2_os) - 1ull));
-    const long long s = (long long)(p >> log2_os) - support / 2 + 1;
-    start = (int)s;
-    return s >= 0 && s <= (long long)(n - support);
+    const unsigned hi = (unsigned)__double2hiint(q), lo = (unsigned)__double2loint(q);
+    const int e = (int)hi >> 20;
+    const unsigned R = (unsigned)((1054 - log2_os) - e);
+    const unsigned xh = __funnelshift_l(lo, hi, 11) | 0x80000000u;
+    const unsigned xl = lo << 11;
+    const unsigned I = __funnelshift_rc(xh, 0u, R);
+    const unsigned F = __funnelshift_rc(xl, xh, R);
+    const unsigned st = __funnelshift_lc(0u, xl, 32u - R);
+    const unsigned G = F | min(st, 1u) | (I & 1u);
+    const unsigned p = I + (G > 0x80000000u ? 1u : 0u);
+    frac = (int)(p & ((1u << log2_os) - 1u));
+    start = (int)(p >> log2_os) - (support / 2 - 1);
+    return (unsigned)start <= (unsigned)(n - support);
 }
 
 struct VisCoords {
@@ -160,6 +172,7 @@ struct degrid_plan {
     int chunk;
     int warps_per_block;
     int blocks_per_sm;
+    int compensated;            // compensated (TwoSum) reduction of the lane partials
     int max_blocks_degrid;      // occupancy results, 0 = not computed yet
     int max_blocks_adjoint;
     int n_slots;                // timing event pairs (0 = timing off)

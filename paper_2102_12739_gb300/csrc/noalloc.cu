@@ -91,6 +91,8 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
     const int l2uv = log2_exact(uv_oversample), l2w = log2_exact(w_oversample);
     if (l2uv < 0 || l2w < 0 || !g_uv || !g_w || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
+    if (((int64_t)(nx > ny ? nx : ny) << l2uv) > ((int64_t)1 << 31) || ((int64_t)nz << l2w) > ((int64_t)1 << 31))
+        return DG_ERR_ARG;
     if (uv_oversample > DG_NOALLOC_MAX_UV_OVERSAMPLE || w_oversample > DG_NOALLOC_MAX_W_OVERSAMPLE ||
         n_subgrids > DG_NOALLOC_MAX_SUBGRIDS || n_vis > DG_NOALLOC_MAX_VIS)
         return DG_ERR_SCRATCH_LIMIT;

@@ -57,18 +57,52 @@ struct Batch {
     long long end;  // end of the chunk
 };
 
+// Bulk prefetch of [p, p + bytes) into L2 (a hint: no completion, no data
+// returned).  Only the 16-byte aligned interior of the range is requested,
+// so nothing outside it is touched.
+__device__ __forceinline__ void prefetch_l2(const void *p, long long bytes)
+{
+    const unsigned long long a = ((unsigned long long)p + 15ull) & ~15ull;
+    const unsigned long long e = ((unsigned long long)p + (unsigned long long)bytes) & ~15ull;
+    if (bytes > 0 && e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
+// Per-visibility input streams of the chunk a warp will work on next: they
+// are prefetched into L2 when its descriptor arrives, a whole chunk before
+// the first load, so the loads of the batch pipeline find them in L2
+// instead of waiting for HBM.
+struct Prefetch {
+    const void *a;      // stream 1 (or nullptr), a_bytes per visibility
+    int a_bytes;
+    const void *b;      // stream 2 (or nullptr)
+    int b_bytes;
+};
+
 // Claims chunks with an atomic counter, one claim ahead: while a warp works
 // on a chunk it already holds the descriptor of the next one, and the atomic
 // for the one after that is in flight.
 struct Claimer {
     const Schedule &sched;
+    Prefetch pf;
     int total;
     int lane;
     int pend;           // lane 0: atomic result not yet consumed
     ChunkDesc next;     // descriptor of the chunk after the current one
     int next_valid;
 
-    __device__ Claimer(const Schedule &sc, int lane_) : sched(sc), lane(lane_)
+    __device__ void prefetch_next() const
+    {
+        if (lane == 0 && next_valid) {
+            if (pf.a)
+                prefetch_l2(static_cast<const char *>(pf.a) + next.lo * pf.a_bytes, (long long)next.n * pf.a_bytes);
+            if (pf.b)
+                prefetch_l2(static_cast<const char *>(pf.b) + next.lo * pf.b_bytes, (long long)next.n * pf.b_bytes);
+        }
+    }
+
+    __device__ Claimer(const Schedule &sc, int lane_, Prefetch pf_ = Prefetch{nullptr, 0, nullptr, 0})
+        : sched(sc), pf(pf_), lane(lane_)
     {
         total = *sc.n_chunks;
         int a = 0, b = 0;
@@ -94,6 +128,7 @@ struct Claimer {
         next_valid = k < total;
         if (next_valid)
             next = sched.chunks[k];
+        prefetch_next();
         if (lane == 0)
             pend = atomicAdd(sched.work_counter, 1);
         bt.s = cur.s;
@@ -170,6 +205,61 @@ __device__ __forceinline__ void issue_batch(const Batch &b, const Coords3 &c, co
         cp_async16(smem_u32(&S.gv[r][4 * half]), guv + (size_t)xv * kUVRow + 4 * half);
     }
     cp_async_commit();
+}
+
+// Rows-only stage of the degridding kernel: the g_u and g_v rows of a batch,
+// 32 bytes per row.  The two 16-byte halves trade places on rows with bit 2
+// set, so that lanes reading the same half of 8 consecutive rows hit 8
+// different bank groups, while each row still fills one contiguous 32-byte
+// slot (its two copies stay one request).
+struct alignas(128) RowStage {
+    float4 u[kBatch][2];
+    float4 v[kBatch][2];
+};
+
+// Slot of half `h` of row `r` in a RowStage row.
+__device__ __forceinline__ int row_half(int r, int h) { return h ^ ((r >> 2) & 1); }
+
+// What issue_rows leaves in registers for the summing step: this lane's
+// visibility's footprint key (-1 when invalid or past the batch) and w row,
+// and whether the whole batch shares lane 0's key and row.
+struct Issued {
+    int key, fw;
+    int key0, fw0;
+    bool uniform;
+};
+
+// Stage 2 of a degridding batch: snap, and copy the g_u / g_v rows into the
+// stage (2 lanes per 32-byte row, so each row is one request).
+__device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, const Geometry &g,
+                                             RowStage &S, const float *__restrict__ guv, int lane,
+                                             DeviceStatus *status)
+{
+    const bool in = lane < b.n;
+    VisCoords vc;
+    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
+    Issued r;
+    r.key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
+    r.fw = valid ? vc.fw : 0;
+    const int fu = valid ? vc.fu : 0, fv = valid ? vc.fv : 0;
+    r.key0 = __shfl_sync(kFull, r.key, 0);
+    r.fw0 = __shfl_sync(kFull, r.fw, 0);
+    // lanes past the end of the batch compute values nobody stores
+    r.uniform = __all_sync(kFull, !in || (r.key == r.key0 && r.fw == r.fw0)) && r.key0 >= 0;
+    const unsigned bad = __ballot_sync(kFull, in && !valid);
+    if (lane == 0 && bad)
+        atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));
+    const int half = lane & 1;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int row = (lane >> 1) + 16 * m;
+        const int xu = __shfl_sync(kFull, fu, row);
+        const int xv = __shfl_sync(kFull, fv, row);
+        cp_async16(smem_u32(&S.u[row][row_half(row, half)]), guv + (size_t)xu * kUVRow + 4 * half);
+        cp_async16(smem_u32(&S.v[row][row_half(row, half)]), guv + (size_t)xv * kUVRow + 4 * half);
+    }
+    cp_async_commit();
+    return r;
 }
 
 // The w table ahead of the per-warp areas in dynamic shared memory.

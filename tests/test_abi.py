@@ -64,10 +64,15 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, a, 8, 10000, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
     assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 2, a, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_UNSUPPORTED
     assert lib.degrid_plan_create(ctypes.byref(h), 512, 512, 4, a, 8, 16384, b, 4, 128, 7, 0) == _native.DG_ERR_DTYPE
+    # an oversampled coordinate n * O beyond 2^31 does not fit the exact 32-bit snap
+    assert lib.degrid_plan_create(ctypes.byref(h), 1 << 18, 8, 4, a, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_UNSUPPORTED
+    assert lib.degrid_plan_create(ctypes.byref(h), 8, 1 << 18, 4, a, 8, 16384, b, 4, 128, 0, 0) == _native.DG_ERR_UNSUPPORTED
     assert h.value is None
     assert lib.degrid_execute(None, None, 1, None, None, None, None, 0, None) == _native.DG_ERR_ARG
     assert lib.grid_adjoint_execute(None, None, 1, None, None, 0, None, None, 0) == _native.DG_ERR_ARG
     assert lib.degrid_coords_execute(None, None, None, 0, None) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_set_compensated(None, 1) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_get_compensated(None, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_tuning(None, 256, 8, 0) == _native.DG_ERR_ARG
     assert lib.degrid_get_status(None, None, None) == _native.DG_ERR_ARG
     assert lib.degrid_pack_subgrids(None, 0, 1, 4, None, None, None) == _native.DG_ERR_DTYPE

@@ -219,6 +219,43 @@ def test_reduced_precision_storage(dtype):
     assert rel_l2(got, ref_q) <= 2e-6
 
 
+@pytest.mark.parametrize("dtype", ["c64", "f16", "bf16"])
+def test_compensated_reduction(dtype):
+    # the compensated form: same bar as the plain one, deterministic, and no
+    # less accurate than the plain sum against the FP64 oracle
+    d = dev()
+    w = small_workload([2500, 0, 1900, 40], kind="mixed", seed=11)
+    w.uvw[7] = [np.inf, 10.0, 1.5]
+    w.uvw[3000] = [20.0, -4.0, 1.5]
+    sub_np = synth.subgrid_stack(4)
+    sub_c64 = torch.from_numpy(sub_np).to(d)
+    if dtype == "c64":
+        sub, scale, ref_sub = sub_c64, None, sub_np.astype(np.complex128)
+    else:
+        sub, scale = dg.pack_subgrids(sub_c64, dtype)
+        codes, sc = oracle.quantize(sub_np, dtype)
+        ref_sub = oracle.dequantize(codes, sc, dtype)
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    with dg.DegridPlan(dtype=dtype, device=d) as plain, \
+            dg.DegridPlan(dtype=dtype, device=d, compensated=True) as comp:
+        assert comp.compensated and not plain.compensated
+        got_p = plain.degrid(sub, uvw, offs, scale=scale).cpu().numpy()
+        got_c = comp.degrid(sub, uvw, offs, scale=scale).cpu().numpy()
+        assert comp.status() == 2           # the count is cleared when read
+        again = comp.degrid(sub, uvw, offs, scale=scale).cpu().numpy()
+        assert comp.status() == 2
+    np.testing.assert_array_equal(got_c.view(np.uint32), again.view(np.uint32))
+    assert got_c[7] == 0 and got_c[3000] == 0
+    ref, bad = oracle.degrid(G_UV, G_W, ref_sub, w.uvw, w.vis_offsets)
+    assert bad == 2
+    # kernel error only (the oracle runs on the values the kernel reads)
+    e_c, e_p = rel_l2(got_c, ref), rel_l2(got_p, ref)
+    assert e_c <= 2e-6
+    assert e_c <= 1.1 * e_p + 1e-9
+    assert rel_l2(got_c, got_p) <= 1e-6
+
+
 # ---------------------------------------------------------------------------
 # adjoint and autograd
 # ---------------------------------------------------------------------------
