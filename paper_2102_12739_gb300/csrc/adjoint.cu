@@ -3,19 +3,22 @@
 //   sub[s][y0+b][x0+a][z0+c] += g_v[b] g_u[a] g_w[c] * vis[i].
 // The weights are real, so this is the exact transpose of degrid.cu.
 //
-// The batch pipeline is the forward kernel's (pipeline.cuh), with the
-// visibility values staged next to the coordinates and GCF rows.  The
-// scatter is factored like the forward sum: for a run of visibilities that
-// share the footprint start and the w-kernel row,
+// The batch pipeline is the forward kernel's (pipeline.cuh): lane i of a
+// batch snaps visibility i, copies its g_u / g_v rows into the warp's stage
+// and loads its value y_i one batch ahead.  The scatter is factored like the
+// forward sum: for a run of visibilities that share the footprint start and
+// the w-kernel row,
 //   sub[y0+b][x0+a][z0+c] += g_w[c] T[b][a],   T[b][a] = sum_i g_v,i[b] g_u,i[a] y_i,
-// so each visibility adds 72 complex x real products into registers and the
-// subgrid is touched only when the run ends.  Each quarter-warp handles one
-// visibility per step (4 per step, 8 steps per batch); lane q of a quarter
-// keeps the column T[0..7][q] of its quarter's partial sum and, when the run
-// ends, flushes it with 32 vector float2 atomics (sub += g_w[c] T[b][q] for
-// c = 0..3, b = 0..7).  Dense lists have runs of hundreds of visibilities, so
-// the atomics are a small fraction of the work; a batch whose 32 visibilities
-// share one run takes a branch-free path.
+// so each visibility adds 64 complex x real products into registers and the
+// subgrid is touched only when the run ends.  Four lanes share a visibility:
+// lane 8j + p keeps the rows T[2j][0..7], T[2j+1][0..7] (32 registers) of the
+// visibilities 8k + p (pass k = 0..3) it handles.  At the end of a run the 8
+// lanes p of each row pair add their partial T through shared memory (a
+// transpose with XOR-swizzled 16-byte slots, free of bank conflicts) and lane
+// 8j + p adds column a = p of rows 2j, 2j+1 to the subgrid with 8 float2
+// atomics (c = 0..3).  Dense lists have runs of hundreds of visibilities, so
+// the atomics are a small fraction of the work.  Batches whose 32
+// visibilities share one run take a branch-free path.
 #include "pipeline.cuh"
 
 namespace dg {
@@ -28,58 +31,65 @@ namespace {
 constexpr int kMaxWarps = 8;
 
 struct alignas(128) WarpSmem {
-    Stage st[2];
+    RowStage st[2];
+    float4 t[8][4][8];          // flush transpose: [p][j][slot a ^ p] = (T[2j][a], T[2j+1][a])
 };
 
-// Column accumulation of one run, owned by one quarter-warp.
-struct Run {
-    float2 T[8];
-    int key;    // footprint start, -1 when nothing is accumulated
-    int fw;
-};
-
-__device__ __forceinline__ void run_reset(Run &R)
+// Visibility value of this lane's visibility in batch b (0 past its end).
+__device__ __forceinline__ float2 load_y(const float2 *__restrict__ vis, const Batch &b, int lane)
 {
-#pragma unroll
-    for (int b = 0; b < 8; ++b)
-        R.T[b] = make_float2(0.f, 0.f);
-    R.key = -1;
+    return lane < b.n ? __ldg(vis + b.b0 + lane) : make_float2(0.f, 0.f);
 }
 
-// sub[y0 + b][x0 + q][z0 + c] += g_w[c] T[b][q] for the run's footprint.
-__device__ __forceinline__ void run_flush(Run &R, float2 *__restrict__ sub_s, int q, const Geometry &g,
-                                          const float4 *wtab, const float *__restrict__ gwt)
+// T[i][a] += g_u[a] * (g_v[2j + i] * y) for the visibility in row r.
+__device__ __forceinline__ void accumulate(float2 (&T)[2][8], const RowStage &S, int r, int j, float2 y)
 {
-    if (R.key < 0)
-        return;
-    const float4 gw = wtab ? wtab[R.fw] : __ldg(reinterpret_cast<const float4 *>(gwt) + R.fw);
-    float2 *col = sub_s + R.key + (int64_t)q * g.nz;
+    const float4 u0 = S.u[r][row_half(r, 0)];
+    const float4 u1 = S.u[r][row_half(r, 1)];
+    const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
+    const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const float2 w0 = make_float2(v.x * y.x, v.x * y.y), w1 = make_float2(v.y * y.x, v.y * y.y);
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        float2 *e = col + (int64_t)b * g.row_stride;
-        const float2 t = R.T[b];
-        atomicAdd(e, make_float2(t.x * gw.x, t.y * gw.x));
-        atomicAdd(e + 1, make_float2(t.x * gw.y, t.y * gw.y));
-        atomicAdd(e + 2, make_float2(t.x * gw.z, t.y * gw.z));
-        atomicAdd(e + 3, make_float2(t.x * gw.w, t.y * gw.w));
+    for (int a = 0; a < 8; ++a) {
+        T[0][a].x = fmaf(gu[a], w0.x, T[0][a].x);
+        T[0][a].y = fmaf(gu[a], w0.y, T[0][a].y);
+        T[1][a].x = fmaf(gu[a], w1.x, T[1][a].x);
+        T[1][a].y = fmaf(gu[a], w1.y, T[1][a].y);
     }
-    run_reset(R);
 }
 
-// T[b] += g_v,r[b] * (g_u,r[q] * y_r): 18 FP32 operations.
-__device__ __forceinline__ void run_add(Run &R, const Stage &S, int r, int q)
+// Adds the run (key, fw) to the subgrid at sub_s and clears T.
+__device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *__restrict__ sub_s,
+                                      int key, int fw, const Geometry &g, const float4 *wtab,
+                                      const float *__restrict__ gwt, int p, int j)
 {
-    const float4 v0 = reinterpret_cast<const float4 *>(S.gv[r])[0];
-    const float4 v1 = reinterpret_cast<const float4 *>(S.gv[r])[1];
-    const float gu = S.gu[r][q];
-    const float2 y = S.y[r];
-    const float wr = y.x * gu, wi = y.y * gu;
-    const float gv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    __syncwarp();                               // previous read-back done
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        R.T[b].x = fmaf(gv[b], wr, R.T[b].x);
-        R.T[b].y = fmaf(gv[b], wi, R.T[b].y);
+    for (int a = 0; a < 8; ++a) {
+        ws.t[p][j][a ^ p] = make_float4(T[0][a].x, T[0][a].y, T[1][a].x, T[1][a].y);
+        T[0][a] = T[1][a] = make_float2(0.f, 0.f);
     }
+    __syncwarp();
+    float4 sum = ws.t[0][j][p];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+        const float4 t = ws.t[q][j][p ^ q];
+        sum.x += t.x;
+        sum.y += t.y;
+        sum.z += t.z;
+        sum.w += t.w;
+    }
+    const float4 gw = wtab ? wtab[fw] : __ldg(reinterpret_cast<const float4 *>(gwt) + fw);
+    float2 *e0 = sub_s + key + (int64_t)p * g.nz + (int64_t)(2 * j) * g.row_stride;
+    float2 *e1 = e0 + g.row_stride;
+    atomicAdd(e0, make_float2(sum.x * gw.x, sum.y * gw.x));
+    atomicAdd(e0 + 1, make_float2(sum.x * gw.y, sum.y * gw.y));
+    atomicAdd(e0 + 2, make_float2(sum.x * gw.z, sum.y * gw.z));
+    atomicAdd(e0 + 3, make_float2(sum.x * gw.w, sum.y * gw.w));
+    atomicAdd(e1, make_float2(sum.z * gw.x, sum.w * gw.x));
+    atomicAdd(e1 + 1, make_float2(sum.z * gw.y, sum.w * gw.y));
+    atomicAdd(e1 + 2, make_float2(sum.z * gw.z, sum.w * gw.z));
+    atomicAdd(e1 + 3, make_float2(sum.z * gw.w, sum.w * gw.w));
 }
 
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_ADJOINT_MIN_BLOCKS)
@@ -91,28 +101,35 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
     WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_raw + wtable_bytes(g))[threadIdx.x >> 5];
     const float4 *wtab = load_wtable(g, gwt, smem_raw);
     const int lane = threadIdx.x & 31;
-    const int quarter = lane >> 3, q = lane & 7;
+    const int p = lane & 7, j = lane >> 3;
 
     Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), vis_in, (int)sizeof(float2)});
     Batch bB = claimer.claim();
     if (bB.n == 0)
         return;
-    issue_batch(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, gwt, wtab, lane, status, vis_in);
+    Issued iB = issue_rows(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
+    float2 yB = load_y(vis_in, bB, lane);
     Batch bC = claimer.advance(bB);
     Coords3 cC = load_uvw(uvw, bC, lane);
 
     int stage = 0;
-    Run R;
-    run_reset(R);
-    int run_s = -1;                     // subgrid of the run in R
+    float2 T[2][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+        T[0][a] = T[1][a] = make_float2(0.f, 0.f);
+    int run_key = -1, run_fw = 0, run_s = -1;   // run being accumulated in T (key -1: none)
     float2 *sub_s = sub_out;
 
     while (bB.n > 0) {
         const Batch bA = bB;
+        const Issued iA = iB;
+        const float2 yA = yB;
         const int sA = stage;
         bB = bC;
-        if (bB.n > 0)
-            issue_batch(bB, cC, g, ws.st[sA ^ 1], guv, gwt, wtab, lane, status, vis_in);
+        if (bB.n > 0) {
+            iB = issue_rows(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
+            yB = load_y(vis_in, bB, lane);
+        }
         bC = claimer.advance(bC);
         cC = load_uvw(uvw, bC, lane);
         if (bB.n > 0)
@@ -121,41 +138,66 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
             cp_async_wait<0>();
         __syncwarp();
 
-        const Stage &S = ws.st[sA];
+        const RowStage &S = ws.st[sA];
         if (bA.s != run_s) {
-            run_flush(R, sub_s, q, g, wtab, gwt);
+            if (run_key >= 0)
+                flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
+            run_key = -1;
             run_s = bA.s;
             sub_s = sub_out + (int64_t)bA.s * g.plane;
         }
-        if (S.uniform) {
-            const int k0 = S.key[0], f0 = S.fw[0];
-            if (k0 != R.key || f0 != R.fw) {
-                run_flush(R, sub_s, q, g, wtab, gwt);
-                R.key = k0;
-                R.fw = f0;
+        if (iA.uniform) {
+            if (iA.key0 != run_key || iA.fw0 != run_fw) {
+                if (run_key >= 0)
+                    flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
+                run_key = iA.key0;
+                run_fw = iA.fw0;
             }
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                run_add(R, S, 4 * t + quarter, q);
+            for (int k = 0; k < 4; ++k) {
+                const int r = 8 * k + p;
+                float2 y;
+                y.x = __shfl_sync(kFull, yA.x, r);
+                y.y = __shfl_sync(kFull, yA.y, r);
+                accumulate(T, S, r, j, y);
+            }
         } else {
+            // visibilities in list order; each change of (footprint, w row)
+            // ends the run; invalid visibilities (key -1) add nothing
 #pragma unroll 1
-            for (int t = 0; t < 8; ++t) {
-                const int r = 4 * t + quarter;
-                const int kv = S.key[r], fv = S.fw[r];
-                if (kv < 0)
-                    continue;
-                if (kv != R.key || fv != R.fw) {
-                    run_flush(R, sub_s, q, g, wtab, gwt);
-                    R.key = kv;
-                    R.fw = fv;
+            for (int k = 0; k < 4; ++k) {
+                const int r = 8 * k + p;
+                const int kr = __shfl_sync(kFull, iA.key, r);
+                const int fr = __shfl_sync(kFull, iA.fw, r);
+                float2 y;
+                y.x = __shfl_sync(kFull, yA.x, r);
+                y.y = __shfl_sync(kFull, yA.y, r);
+                bool done = kr < 0;
+#pragma unroll 1
+                while (true) {
+                    const unsigned todo = __ballot_sync(kFull, !done);
+                    if (todo == 0)
+                        break;
+                    const int leader = __ffs(todo) - 1;
+                    const int lk = __shfl_sync(kFull, kr, leader);
+                    const int lf = __shfl_sync(kFull, fr, leader);
+                    if (lk != run_key || lf != run_fw) {
+                        if (run_key >= 0)
+                            flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
+                        run_key = lk;
+                        run_fw = lf;
+                    }
+                    const bool mine = !done && kr == lk && fr == lf;
+                    accumulate(T, S, r, j, mine ? y : make_float2(0.f, 0.f));
+                    done = done || mine;
                 }
-                run_add(R, S, r, q);
             }
         }
         __syncwarp();
         stage ^= 1;
     }
-    run_flush(R, sub_s, q, g, wtab, gwt);
+    if (run_key >= 0)
+        flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
 }
 
 size_t smem_bytes(const degrid_plan *p)

@@ -278,6 +278,27 @@ def test_adjoint_matches_oracle(plan):
         assert rel_l2(acc - 1, ref) <= TOL["c64"]
 
 
+@pytest.mark.parametrize("kind", ["line", "scatter", "mixed"])
+def test_adjoint_all_list_kinds_with_invalid_points(kind):
+    # runs of every length (scatter: a new footprint at nearly every
+    # visibility), ragged batch tails, an empty subgrid, invalid points
+    d = dev()
+    shape = (40, 72, 4)
+    w = small_workload([1033, 0, 64, 517], kind=kind, shape=shape, seed=21)
+    w.uvw[3] = [np.nan, 10.0, 1.5]
+    w.uvw[1040] = [20.0, 80.0, 1.5]
+    w.uvw[1200] = [10.0, 10.0, 2.5]
+    y = synth.adjoint_vis(w.n_vis)
+    with dg.DegridPlan(shape=shape, device=d) as p:
+        got = p.grid(torch.from_numpy(y).to(d), torch.from_numpy(w.uvw).to(d),
+                     torch.from_numpy(w.vis_offsets).to(d), w.n_subgrids).cpu().numpy()
+        assert p.status() == 3
+    ref, bad = oracle.grid(G_UV, G_W, shape, w.n_subgrids, w.uvw, w.vis_offsets, y)
+    assert bad == 3
+    assert rel_l2(got, ref) <= TOL["c64"]
+    assert np.all(got[1] == 0)                   # the empty subgrid stays zero
+
+
 def test_adjoint_dot_product_identity_on_gpu(plan):
     d = dev()
     w = synth.workload("line1_20k")
