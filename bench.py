@@ -41,9 +41,9 @@ WORKLOAD_DESC = ("64 subgrids of 512x512x4 complex64 (i.i.d. complex Gaussian), 
                  "oversampling 128")
 FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 4 flop)
 # DRAM bytes (read + write) per visibility of degrid_kernel<DG_C64>, from one ncu capture
-# (profiles/degrid_kernel_lines16_250k_ncu.md: 4,000,000 visibilities; the traffic is uvw,
-# output and footprints, all proportional to the visibilities).  Valid only for the kernel
-# sources it was taken on: the bench reports null traffic once they change.
+# of the 4,000,000-visibility case lines16_250k (the traffic is uvw, output and footprints,
+# all proportional to the visibilities).  Valid only for the kernel sources it was taken
+# on: the bench reports null traffic once they change.
 TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
                           "paper_2102_12739_gb300/csrc/pipeline.cuh",
                           "paper_2102_12739_gb300/csrc/internal.cuh")
