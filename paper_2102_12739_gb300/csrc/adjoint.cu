@@ -48,13 +48,12 @@ __device__ __forceinline__ void accumulate(float2 (&T)[2][8], const RowStage &S,
     const float4 u1 = S.u[r][row_half(r, 1)];
     const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
     const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-    const float2 w0 = make_float2(v.x * y.x, v.x * y.y), w1 = make_float2(v.y * y.x, v.y * y.y);
+    const float2 w0 = __fmul2_rn(y, make_float2(v.x, v.x)), w1 = __fmul2_rn(y, make_float2(v.y, v.y));
+    // packed (re, im) FMAs with a duplicated real weight (bitwise two scalar FMAs)
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-        T[0][a].x = fmaf(gu[a], w0.x, T[0][a].x);
-        T[0][a].y = fmaf(gu[a], w0.y, T[0][a].y);
-        T[1][a].x = fmaf(gu[a], w1.x, T[1][a].x);
-        T[1][a].y = fmaf(gu[a], w1.y, T[1][a].y);
+        T[0][a] = __ffma2_rn(make_float2(gu[a], gu[a]), w0, T[0][a]);
+        T[1][a] = __ffma2_rn(make_float2(gu[a], gu[a]), w1, T[1][a]);
     }
 }
 

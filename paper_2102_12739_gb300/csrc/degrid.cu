@@ -2,12 +2,15 @@
 // variants), re-designed for sm_103a.
 //
 // Work decomposition (pipeline.cuh).  A persistent grid of warps walks chunks
-// of consecutive visibilities of one subgrid in batches of 32.  Per batch
-// three stages overlap across consecutive batches of a warp:
-//  1. the FP64 coordinates of batch n + 2 are loaded into registers;
-//  2. batch n + 1 is snapped (one visibility per lane) and its g_u and g_v
-//     rows are copied into the warp's shared-memory stage with cp.async;
-//  3. batch n is summed from the stage that arrived.
+// of consecutive visibilities of one subgrid in steps of 64 (two halves of
+// 32, which amortises the per-step bookkeeping and gives every lane two
+// independent coordinates to snap).  Three stages overlap across consecutive
+// steps of a warp:
+//  1. the FP64 coordinates of step n + 2 are loaded into registers (and the
+//     next chunk's are prefetched into L2 when its descriptor arrives);
+//  2. step n + 1 is snapped (one visibility per lane and half) and its g_u and
+//     g_v rows are copied into the warp's shared-memory stage with cp.async;
+//  3. step n is summed from the stage that arrived, one half after the other.
 //
 // Footprint sum.  The separable weights let the 8 x 8 x 4 sum be taken in
 // three contractions,
@@ -21,32 +24,34 @@
 // holds the rows M[2j][0..7] and M[2j+1][0..7] of the footprint in 32
 // registers and, for a visibility r, forms
 // sum_{b = 2j, 2j+1} g_v[b] sum_a g_u[a] M[b][a] (36 FP32 operations).  A
-// batch takes four passes; in pass k lane 8j + p works on visibility
+// half takes four passes; in pass k lane 8j + p works on visibility
 // 8 (k ^ j) + p, an order chosen so that the two exchange steps of the
 // reduction move the same pass slots on every lane (no selects): lane xor 16
 // adds slots 2, 3 to 0, 1, then lane xor 8 adds slot 1 to slot 0, and lane
 // 8j + p ends with visibility 8j + p, so the warp writes its 32 results into
 // one contiguous 256-byte segment in lane order.  The 8 lanes of one 128-bit
 // shared-memory wavefront read 8 consecutive rows of the stage, which its
-// half-swapped layout places in 8 different bank groups.  M is built by the whole warp (two
-// entries per lane) into shared memory and read back by rows; a batch whose
-// 32 visibilities share one footprint and w row needs no checks, and any
-// other batch is summed once per distinct (footprint, w row) it holds, every
-// lane keeping the pass that matches its own visibility.
-// Scalar FP32 FMAs: packed FFMA2 with three distinct register pairs ran at
-// about half the FP32 peak on this part.
+// half-swapped layout places in 8 different bank groups.  M is built by the
+// whole warp (two entries per lane) into shared memory and read back by rows;
+// a half whose 32 visibilities share one footprint and w row needs no checks,
+// and any other half is summed once per distinct (footprint, w row) it holds,
+// every lane keeping the pass that matches its own visibility.
+// The products use packed FFMA2 on (re, im) pairs with a duplicated real
+// weight: bitwise the same as two scalar FMAs, in half the instructions
+// (11.2 instead of 12.7 warp instructions per visibility on dense lines).
 #include "pipeline.cuh"
 
 namespace dg {
 namespace {
 
 #ifndef DG_DEGRID_MIN_BLOCKS
-#define DG_DEGRID_MIN_BLOCKS 3   // resident CTAs per SM the register budget is sized for
+#define DG_DEGRID_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for
 #endif
 
 constexpr int kMaxWarps = 8;                // per CTA
+constexpr int kBatchVis = 2 * kBatch;       // visibilities per pipeline step (two halves)
 struct alignas(128) WarpSmem {
-    RowStage st[2];
+    RowStage st[2][2];          // [stage][half]
     float2 m[8][8];             // M[b][a] of the footprint being built
     float2 part[4][kWarp];      // per-pass partials on the mixed path
 };
@@ -93,16 +98,16 @@ __device__ __forceinline__ float2 quarter_sum(const float2 (&M)[2][8], const Row
     const float4 u1 = S.u[r][row_half(r, 1)];
     const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
     const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-    float2 t0 = make_float2(M[0][0].x * gu[0], M[0][0].y * gu[0]);
-    float2 t1 = make_float2(M[1][0].x * gu[0], M[1][0].y * gu[0]);
+    // complex x real products as packed pairs (re, im) * (g, g): one FFMA2
+    // per product, each half rounded exactly as a scalar FMA
+    float2 t0 = __fmul2_rn(M[0][0], make_float2(gu[0], gu[0]));
+    float2 t1 = __fmul2_rn(M[1][0], make_float2(gu[0], gu[0]));
 #pragma unroll
     for (int a = 1; a < 8; ++a) {
-        t0.x = fmaf(M[0][a].x, gu[a], t0.x);
-        t0.y = fmaf(M[0][a].y, gu[a], t0.y);
-        t1.x = fmaf(M[1][a].x, gu[a], t1.x);
-        t1.y = fmaf(M[1][a].y, gu[a], t1.y);
+        t0 = __ffma2_rn(M[0][a], make_float2(gu[a], gu[a]), t0);
+        t1 = __ffma2_rn(M[1][a], make_float2(gu[a], gu[a]), t1);
     }
-    return make_float2(fmaf(t1.x, v.y, t0.x * v.x), fmaf(t1.y, v.y, t0.y * v.x));
+    return __ffma2_rn(t1, make_float2(v.y, v.y), __fmul2_rn(t0, make_float2(v.x, v.x)));
 }
 
 // Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
@@ -112,6 +117,106 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e)
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return s;
+}
+
+// State of the cached footprint matrix: rows 2j, 2j + 1 of M for (key, fw)
+// in the subgrid at `base` (key -2: none).
+struct MState {
+    float2 M[2][8];
+    int key, fw;
+};
+
+// Sums one half batch (32 visibilities, stage S, issued info I), reduces the
+// four lane partials and stores visibility `lane` of the half.
+template <int DT, bool COMP>
+__device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStage &S, const Issued &I,
+                                         const Batch &h, const void *__restrict__ subgrids, int64_t base,
+                                         float sc, const Geometry &g, const float4 *wtab,
+                                         const float *__restrict__ gwt, float2 *__restrict__ vis_out,
+                                         int lane, int p, int j)
+{
+    float2 P[4];                        // pass k: this lane's quarter of visibility 8 (k ^ j) + p
+    if (I.uniform) {
+        if (I.key0 != ms.key || I.fw0 != ms.fw) {
+            const float4 gw = wtab ? wtab[I.fw0] : __ldg(reinterpret_cast<const float4 *>(gwt) + I.fw0);
+            build_rows<DT>(ms.M, ws.m, subgrids, base, I.key0, gw, g, lane, j);
+            ms.key = I.key0;
+            ms.fw = I.fw0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            P[k] = quarter_sum(ms.M, S, 8 * (k ^ j) + p, j);
+    } else {
+        // Pass k covers visibilities 8k .. 8k + 7 here, so a change of
+        // footprint inside a run of the list touches one pass.  Each pass is
+        // summed once per distinct (footprint, w row) among its visibilities,
+        // every lane keeping the sum that matches its own (invalid ones, key
+        // -1, stay zero); the partials then move to the slots of the permuted
+        // order, slot k = pass k ^ j.
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * k + p;
+            const int kr = __shfl_sync(kFull, I.key, r);
+            const int fr = __shfl_sync(kFull, I.fw, r);
+            bool done = kr < 0;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+            while (true) {
+                const unsigned todo = __ballot_sync(kFull, !done);
+                if (todo == 0)
+                    break;
+                const int leader = __ffs(todo) - 1;
+                const int lk = __shfl_sync(kFull, kr, leader);
+                const int lf = __shfl_sync(kFull, fr, leader);
+                if (lk != ms.key || lf != ms.fw) {
+                    const float4 gw = wtab ? wtab[lf] : __ldg(reinterpret_cast<const float4 *>(gwt) + lf);
+                    build_rows<DT>(ms.M, ws.m, subgrids, base, lk, gw, g, lane, j);
+                    ms.key = lk;
+                    ms.fw = lf;
+                }
+                const float2 x = quarter_sum(ms.M, S, r, j);
+                const bool mine = !done && kr == lk && fr == lf;
+                if (mine)
+                    acc = x;
+                done = done || mine;
+            }
+            ws.part[k][lane] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            P[k] = ws.part[k ^ j][lane];
+        __syncwarp();
+    }
+    // lane xor 16 (j ^ 2) brings slots 2, 3 onto 0, 1; lane xor 8 (j ^ 1)
+    // brings slot 1 onto 0
+    float2 V;
+    if (COMP) {
+        // the same three additions as error-free sums; the four rounding
+        // errors are summed and added back once
+        float2 e0, e1, e;
+        P[0].x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[2].x, 16), e0.x);
+        P[0].y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[2].y, 16), e0.y);
+        P[1].x = two_sum(P[1].x, __shfl_xor_sync(kFull, P[3].x, 16), e1.x);
+        P[1].y = two_sum(P[1].y, __shfl_xor_sync(kFull, P[3].y, 16), e1.y);
+        V.x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[1].x, 8), e.x);
+        V.y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[1].y, 8), e.y);
+        e.x += e0.x + __shfl_xor_sync(kFull, e1.x, 8);
+        e.y += e0.y + __shfl_xor_sync(kFull, e1.y, 8);
+        V.x += e.x;
+        V.y += e.y;
+    } else {
+        P[0].x += __shfl_xor_sync(kFull, P[2].x, 16);
+        P[0].y += __shfl_xor_sync(kFull, P[2].y, 16);
+        P[1].x += __shfl_xor_sync(kFull, P[3].x, 16);
+        P[1].y += __shfl_xor_sync(kFull, P[3].y, 16);
+        V.x = P[0].x + __shfl_xor_sync(kFull, P[1].x, 8);
+        V.y = P[0].y + __shfl_xor_sync(kFull, P[1].y, 8);
+    }
+    if (DT != DG_C64)
+        V = __fmul2_rn(V, make_float2(sc, sc));
+    if (lane < h.n)                     // lane 8j + p holds visibility 8j + p of the half
+        vis_out[h.b0 + lane] = V;
 }
 
 template <int DT, bool COMP>
@@ -128,129 +233,61 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     const int lane = threadIdx.x & 31;
     const int p = lane & 7, j = lane >> 3;
 
-    Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), nullptr, 0});
+    ClaimerT<kBatchVis> claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), nullptr, 0});
     Batch bB = claimer.claim();         // rows in flight
     if (bB.n == 0)
         return;
-    Issued iB = issue_rows(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
+    Issued iB0 = issue_rows(half_of(bB, 0), load_uvw(uvw, half_of(bB, 0), lane), g, ws.st[0][0], guv,
+                            lane, status, false);
+    Issued iB1 = issue_rows(half_of(bB, 1), load_uvw(uvw, half_of(bB, 1), lane), g, ws.st[0][1], guv,
+                            lane, status, true);
     Batch bC = claimer.advance(bB);     // coordinates in registers
-    Coords3 cC = load_uvw(uvw, bC, lane);
+    Coords3 cC0 = load_uvw(uvw, half_of(bC, 0), lane);
+    Coords3 cC1 = load_uvw(uvw, half_of(bC, 1), lane);
 
     int stage = 0;
-    float2 M[2][8];                     // rows 2j, 2j + 1 of M for (m_key, m_fw) in subgrid m_s
-    int m_key = -2, m_fw = -1, m_s = -1;
+    MState ms;
+    ms.key = -2;
+    ms.fw = -1;
+    int m_s = -1;
     int64_t base = 0;
     float sc = 1.f;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int a = 0; a < 8; ++a)
-            M[i][a] = make_float2(0.f, 0.f);
+            ms.M[i][a] = make_float2(0.f, 0.f);
 
     while (bB.n > 0) {
         const Batch bA = bB;            // summed in this iteration
-        const Issued iA = iB;
+        const Issued iA0 = iB0, iA1 = iB1;
         const int sA = stage;
         bB = bC;
-        if (bB.n > 0)
-            iB = issue_rows(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
+        if (bB.n > 0) {
+            iB0 = issue_rows(half_of(bB, 0), cC0, g, ws.st[sA ^ 1][0], guv, lane, status, false);
+            iB1 = issue_rows(half_of(bB, 1), cC1, g, ws.st[sA ^ 1][1], guv, lane, status, true);
+        }
         bC = claimer.advance(bC);
-        cC = load_uvw(uvw, bC, lane);
+        cC0 = load_uvw(uvw, half_of(bC, 0), lane);
+        cC1 = load_uvw(uvw, half_of(bC, 1), lane);
         if (bB.n > 0)
             cp_async_wait<1>();         // the stage of batch A; batch B may stay in flight
         else
             cp_async_wait<0>();
         __syncwarp();
 
-        const RowStage &S = ws.st[sA];
         if (bA.s != m_s) {
             m_s = bA.s;
-            m_key = -2;
+            ms.key = -2;
             base = (int64_t)bA.s * g.plane;
             if (DT != DG_C64)
                 sc = __ldg(scale + bA.s);
         }
-        float2 P[4];                    // pass k: this lane's quarter of visibility 8 (k ^ j) + p
-        if (iA.uniform) {
-            if (iA.key0 != m_key || iA.fw0 != m_fw) {
-                const float4 gw = wtab ? wtab[iA.fw0] : __ldg(reinterpret_cast<const float4 *>(gwt) + iA.fw0);
-                build_rows<DT>(M, ws.m, subgrids, base, iA.key0, gw, g, lane, j);
-                m_key = iA.key0;
-                m_fw = iA.fw0;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                P[k] = quarter_sum(M, S, 8 * (k ^ j) + p, j);
-        } else {
-            // Pass k covers visibilities 8k .. 8k + 7 here, so a change of
-            // footprint inside a run of the list touches one pass.  Each pass
-            // is summed once per distinct (footprint, w row) among its
-            // visibilities, every lane keeping the sum that matches its own
-            // (invalid ones, key -1, stay zero); the partials then move to
-            // the slots of the permuted order, slot k = pass k ^ j.
-#pragma unroll 1
-            for (int k = 0; k < 4; ++k) {
-                const int r = 8 * k + p;
-                const int kr = __shfl_sync(kFull, iA.key, r);
-                const int fr = __shfl_sync(kFull, iA.fw, r);
-                bool done = kr < 0;
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll 1
-                while (true) {
-                    const unsigned todo = __ballot_sync(kFull, !done);
-                    if (todo == 0)
-                        break;
-                    const int leader = __ffs(todo) - 1;
-                    const int lk = __shfl_sync(kFull, kr, leader);
-                    const int lf = __shfl_sync(kFull, fr, leader);
-                    if (lk != m_key || lf != m_fw) {
-                        const float4 gw = wtab ? wtab[lf] : __ldg(reinterpret_cast<const float4 *>(gwt) + lf);
-                        build_rows<DT>(M, ws.m, subgrids, base, lk, gw, g, lane, j);
-                        m_key = lk;
-                        m_fw = lf;
-                    }
-                    const float2 x = quarter_sum(M, S, r, j);
-                    const bool mine = !done && kr == lk && fr == lf;
-                    if (mine)
-                        acc = x;
-                    done = done || mine;
-                }
-                ws.part[k][lane] = acc;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                P[k] = ws.part[k ^ j][lane];
-        }
-        // lane xor 16 (j ^ 2) brings slots 2, 3 onto 0, 1; lane xor 8 (j ^ 1)
-        // brings slot 1 onto 0
-        float2 V;
-        if (COMP) {
-            // the same three additions as error-free sums; the four rounding
-            // errors are summed and added back once
-            float2 e0, e1, e;
-            P[0].x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[2].x, 16), e0.x);
-            P[0].y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[2].y, 16), e0.y);
-            P[1].x = two_sum(P[1].x, __shfl_xor_sync(kFull, P[3].x, 16), e1.x);
-            P[1].y = two_sum(P[1].y, __shfl_xor_sync(kFull, P[3].y, 16), e1.y);
-            V.x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[1].x, 8), e.x);
-            V.y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[1].y, 8), e.y);
-            e.x += e0.x + __shfl_xor_sync(kFull, e1.x, 8);
-            e.y += e0.y + __shfl_xor_sync(kFull, e1.y, 8);
-            V.x += e.x;
-            V.y += e.y;
-        } else {
-            P[0].x += __shfl_xor_sync(kFull, P[2].x, 16);
-            P[0].y += __shfl_xor_sync(kFull, P[2].y, 16);
-            P[1].x += __shfl_xor_sync(kFull, P[3].x, 16);
-            P[1].y += __shfl_xor_sync(kFull, P[3].y, 16);
-            V.x = P[0].x + __shfl_xor_sync(kFull, P[1].x, 8);
-            V.y = P[0].y + __shfl_xor_sync(kFull, P[1].y, 8);
-        }
-        if (DT != DG_C64)
-            V = __fmul2_rn(V, make_float2(sc, sc));
-        if (lane < bA.n)                // lane 8j + p holds visibility 8j + p
-            vis_out[bA.b0 + lane] = V;
+        sum_half<DT, COMP>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g, wtab, gwt,
+                           vis_out, lane, p, j);
+        if (bA.n > kBatch)
+            sum_half<DT, COMP>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc, g, wtab,
+                               gwt, vis_out, lane, p, j);
         __syncwarp();
         stage ^= 1;
     }

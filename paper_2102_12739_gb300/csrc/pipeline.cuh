@@ -3,10 +3,10 @@
 // A persistent grid of warps claims chunks of consecutive visibilities of
 // one subgrid (schedule.cu; claims pipelined one chunk ahead) and walks each
 // chunk in batches of 32.  For every batch, lane i snaps visibility i (exact
-// integer rint of its FP64 coordinates, internal.cuh), records its footprint
-// key and w-kernel row, and copies its g_u and g_v rows into the warp's
-// shared-memory stage with cp.async; the small w table is kept in the CTA's
-// shared memory.  The paper's D1 likewise computes the coordinates of all
+// integer rint of its FP64 coordinates, internal.cuh), keeps its footprint
+// key and w-kernel row in registers, and copies its g_u and g_v rows into
+// the warp's shared-memory stage with cp.async; the small w table is kept in
+// the CTA's shared memory.  The paper's D1 likewise computes the coordinates of all
 // N_b visibilities of a block cooperatively into shared memory before the
 // sums (Section "Implementation").
 #pragma once
@@ -19,16 +19,6 @@ namespace {
 constexpr int kBatch = 32;                  // visibilities per batch
 constexpr int kUVRow = 8;                   // floats per uv table row (32 B)
 constexpr int kWRow = 4;                    // floats per w table row (16 B)
-
-struct alignas(128) Stage {
-    float gu[kBatch][kUVRow];   // g_uv[fu], per visibility
-    float gv[kBatch][kUVRow];   // g_uv[fv]
-    float gw[kBatch][kWRow];    // g_w[fw]
-    int key[kBatch];            // footprint start (y0 * nx + x0) * nz + z0, -1 invalid
-    int fw[kBatch];             // w-kernel row
-    float2 y[kBatch];           // visibility values (gridding only)
-    int uniform;                // all 32 share one valid footprint and one w row
-};
 
 // ---- PTX wrappers ---------------------------------------------------------
 
@@ -81,8 +71,9 @@ struct Prefetch {
 
 // Claims chunks with an atomic counter, one claim ahead: while a warp works
 // on a chunk it already holds the descriptor of the next one, and the atomic
-// for the one after that is in flight.
-struct Claimer {
+// for the one after that is in flight.  Batches of kStep visibilities.
+template <int kStep>
+struct ClaimerT {
     const Schedule &sched;
     Prefetch pf;
     int total;
@@ -101,7 +92,7 @@ struct Claimer {
         }
     }
 
-    __device__ Claimer(const Schedule &sc, int lane_, Prefetch pf_ = Prefetch{nullptr, 0, nullptr, 0})
+    __device__ ClaimerT(const Schedule &sc, int lane_, Prefetch pf_ = Prefetch{nullptr, 0, nullptr, 0})
         : sched(sc), pf(pf_), lane(lane_)
     {
         total = *sc.n_chunks;
@@ -134,7 +125,7 @@ struct Claimer {
         bt.s = cur.s;
         bt.b0 = cur.lo;
         bt.end = cur.lo + cur.n;
-        bt.n = (int)min((long long)kBatch, bt.end - bt.b0);
+        bt.n = (int)min((long long)kStep, bt.end - bt.b0);
         return bt;
     }
 
@@ -143,13 +134,24 @@ struct Claimer {
         if (b.n == 0)
             return b;
         Batch nb = b;
-        nb.b0 = b.b0 + kBatch;
+        nb.b0 = b.b0 + kStep;
         if (nb.b0 >= b.end)
             return claim();
-        nb.n = (int)min((long long)kBatch, b.end - nb.b0);
+        nb.n = (int)min((long long)kStep, b.end - nb.b0);
         return nb;
     }
 };
+
+using Claimer = ClaimerT<kBatch>;
+
+// The visibilities [b0 + 32h, b0 + 32h + 32) of a batch of 64.
+__device__ __forceinline__ Batch half_of(const Batch &b, int h)
+{
+    Batch r = b;
+    r.b0 = b.b0 + kBatch * h;
+    r.n = max(0, min(kBatch, b.n - kBatch * h));
+    return r;
+}
 
 struct Coords3 {
     double u, v, w;
@@ -167,58 +169,21 @@ __device__ __forceinline__ Coords3 load_uvw(const double *__restrict__ uvw, cons
     return c;
 }
 
-// Stage 2 of a batch: coordinates, keys, w rows and the copies of the g_u /
-// g_v rows (2 lanes per 32-byte row); with `vis`, also the visibility values.
-__device__ __forceinline__ void issue_batch(const Batch &b, const Coords3 &c, const Geometry &g,
-                                            Stage &S, const float *__restrict__ guv,
-                                            const float *__restrict__ gwt, const float4 *wtab,
-                                            int lane, DeviceStatus *status,
-                                            const float2 *__restrict__ vis = nullptr)
-{
-    const bool in = lane < b.n;
-    VisCoords vc;
-    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
-    const int key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
-    const int fu = valid ? vc.fu : 0, fv = valid ? vc.fv : 0, fw = valid ? vc.fw : 0;
-    S.key[lane] = key;
-    S.fw[lane] = fw;
-    if (vis)
-        S.y[lane] = in ? __ldg(vis + b.b0 + lane) : make_float2(0.f, 0.f);
-    const int key0 = __shfl_sync(kFull, key, 0), fw0 = __shfl_sync(kFull, fw, 0);
-    const bool uniform = __all_sync(kFull, key == key0 && fw == fw0) && key0 >= 0;
-    if (lane == 0)
-        S.uniform = uniform;
-    const unsigned bad = __ballot_sync(kFull, in && !valid);
-    if (lane == 0 && bad)
-        atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));
-    if (wtab)
-        reinterpret_cast<float4 *>(S.gw)[lane] = wtab[fw];
-    else
-        cp_async16(smem_u32(S.gw[lane]), gwt + (size_t)fw * kWRow);
-    const int half = lane & 1;
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const int r = (lane >> 1) + 16 * m;
-        const int xu = __shfl_sync(kFull, fu, r);
-        const int xv = __shfl_sync(kFull, fv, r);
-        cp_async16(smem_u32(&S.gu[r][4 * half]), guv + (size_t)xu * kUVRow + 4 * half);
-        cp_async16(smem_u32(&S.gv[r][4 * half]), guv + (size_t)xv * kUVRow + 4 * half);
-    }
-    cp_async_commit();
-}
-
-// Rows-only stage of the degridding kernel: the g_u and g_v rows of a batch,
-// 32 bytes per row.  The two 16-byte halves trade places on rows with bit 2
-// set, so that lanes reading the same half of 8 consecutive rows hit 8
-// different bank groups, while each row still fills one contiguous 32-byte
-// slot (its two copies stay one request).
+// Row stage: the g_u and g_v rows of 32 visibilities, 32 bytes per row.  The
+// two 16-byte halves trade places on rows with bit 2 set, so that lanes
+// reading the same half of 8 consecutive rows hit 8 different bank groups,
+// while each row still fills one contiguous 32-byte slot (its two copies stay
+// one L2 request).  (A 48-byte padded row stride also avoids the conflicts
+// with fixed half offsets, but its larger footprint took L1 capacity from
+// the coordinate loads and ran slower.)
 struct alignas(128) RowStage {
     float4 u[kBatch][2];
     float4 v[kBatch][2];
+    __device__ static int slot(int r, int h) { return h ^ ((r >> 2) & 1); }
 };
 
 // Slot of half `h` of row `r` in a RowStage row.
-__device__ __forceinline__ int row_half(int r, int h) { return h ^ ((r >> 2) & 1); }
+__device__ __forceinline__ int row_half(int r, int h) { return RowStage::slot(r, h); }
 
 // What issue_rows leaves in registers for the summing step: this lane's
 // visibility's footprint key (-1 when invalid or past the batch) and w row,
@@ -231,9 +196,10 @@ struct Issued {
 
 // Stage 2 of a degridding batch: snap, and copy the g_u / g_v rows into the
 // stage (2 lanes per 32-byte row, so each row is one request).
+template <class Stage>
 __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, const Geometry &g,
-                                             RowStage &S, const float *__restrict__ guv, int lane,
-                                             DeviceStatus *status)
+                                             Stage &S, const float *__restrict__ guv, int lane,
+                                             DeviceStatus *status, bool commit = true)
 {
     const bool in = lane < b.n;
     VisCoords vc;
@@ -255,10 +221,11 @@ __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, c
         const int row = (lane >> 1) + 16 * m;
         const int xu = __shfl_sync(kFull, fu, row);
         const int xv = __shfl_sync(kFull, fv, row);
-        cp_async16(smem_u32(&S.u[row][row_half(row, half)]), guv + (size_t)xu * kUVRow + 4 * half);
-        cp_async16(smem_u32(&S.v[row][row_half(row, half)]), guv + (size_t)xv * kUVRow + 4 * half);
+        cp_async16(smem_u32(&S.u[row][Stage::slot(row, half)]), guv + (size_t)xu * kUVRow + 4 * half);
+        cp_async16(smem_u32(&S.v[row][Stage::slot(row, half)]), guv + (size_t)xv * kUVRow + 4 * half);
     }
-    cp_async_commit();
+    if (commit)
+        cp_async_commit();
     return r;
 }
 
