@@ -133,6 +133,28 @@ dg_status degrid_plan_set_tuning(degrid_plan_t plan, int chunk, int warps_per_bl
 dg_status degrid_plan_set_compensated(degrid_plan_t plan, int enabled);
 dg_status degrid_plan_get_compensated(degrid_plan_t plan, int *enabled);
 
+/*
+ * Summing arm for short runs (the paper's per-visibility kernels D1/D2 next
+ * to the footprint-reuse path, Section "Implementation").  degrid_execute
+ * works on halves of 32 consecutive visibilities.  A half whose visibilities
+ * share one footprint and w row reuses the cached footprint sum M; any other
+ * half with at least min_runs runs of equal (footprint, w row) is summed
+ * directly, every visibility from its own 8 x 8 x 4 footprint (no cache
+ * rebuilds), and halves with fewer runs rebuild M per run.  Both arms do the
+ * same arithmetic in the same order, so the results are bitwise identical;
+ * only the speed differs: the direct arm wins on lists whose footprints
+ * overlap but change often (w rows changing every few visibilities) and
+ * loses on footprints scattered over the subgrid.  min_runs: 1 ..
+ * DG_DIRECT_RUNS_NEVER (33: never, the default; a plan with the arm enabled
+ * launches another instance of the kernel).  DG_DIRECT_RUNS_SHORT is the
+ * setting the autotuner tries.  Returns DG_OK or DG_ERR_ARG.
+ */
+#define DG_DIRECT_RUNS_NEVER 33
+#define DG_DIRECT_RUNS_DEFAULT DG_DIRECT_RUNS_NEVER
+#define DG_DIRECT_RUNS_SHORT 9
+dg_status degrid_plan_set_direct_runs(degrid_plan_t plan, int min_runs);
+dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
+
 /* Read back the current tuning (any pointer may be NULL). */
 dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_block,
                                  int *blocks_per_sm);

@@ -140,7 +140,8 @@ class DegridPlan:
         c, w, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(load().degrid_plan_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(w),
                                             ctypes.byref(b)), "degrid_plan_get_tuning")
-        return {"chunk": c.value, "warps_per_block": w.value, "blocks_per_sm": b.value}
+        return {"chunk": c.value, "warps_per_block": w.value, "blocks_per_sm": b.value,
+                "direct_runs": self.direct_runs}
 
     def set_compensated(self, enabled: bool = True) -> None:
         """Compensated (TwoSum) reduction of the lane partials in degrid()."""
@@ -153,6 +154,20 @@ class DegridPlan:
         check(load().degrid_plan_get_compensated(self.handle, ctypes.byref(v)),
               "degrid_plan_get_compensated")
         return bool(v.value)
+
+    def set_direct_runs(self, min_runs: int) -> None:
+        """Halves of 32 visibilities with at least min_runs footprint runs are
+        summed directly instead of through the footprint cache (1..33; 33 =
+        never).  Results are bitwise the same either way."""
+        check(load().degrid_plan_set_direct_runs(self.handle, int(min_runs)),
+              "degrid_plan_set_direct_runs")
+
+    @property
+    def direct_runs(self) -> int:
+        v = ctypes.c_int()
+        check(load().degrid_plan_get_direct_runs(self.handle, ctypes.byref(v)),
+              "degrid_plan_get_direct_runs")
+        return v.value
 
     def enable_timing(self, n_slots: int = 4096) -> None:
         """Record a CUDA event pair around the main kernel of each of the next

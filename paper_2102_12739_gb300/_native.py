@@ -26,6 +26,10 @@ DG_C64 = 0
 DG_C32_F16 = 1
 DG_C32_BF16 = 2
 
+DG_DIRECT_RUNS_NEVER = 33
+DG_DIRECT_RUNS_DEFAULT = DG_DIRECT_RUNS_NEVER
+DG_DIRECT_RUNS_SHORT = 9
+
 # name -> (restype, argtypes); mirrors include/degrid.h
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -38,6 +42,8 @@ SIGNATURES = {
     "degrid_plan_set_tuning": (_I, [_P, _I, _I, _I]),
     "degrid_plan_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "degrid_plan_set_compensated": (_I, [_P, _I]),
+    "degrid_plan_set_direct_runs": (_I, [_P, _I]),
+    "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_get_compensated": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_enable_timing": (_I, [_P, _I]),
     "degrid_plan_kernel_times_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I,

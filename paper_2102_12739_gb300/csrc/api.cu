@@ -232,6 +232,7 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     p->chunk = 256;
     p->warps_per_block = dg_max_warps_per_block();
     p->blocks_per_sm = 0;
+    p->direct_runs = DG_DIRECT_RUNS_DEFAULT;
 
     dg_status st = DG_OK;
     std::vector<float> h_uv((size_t)uv_oversample * uv_support), h_w((size_t)w_oversample * w_support);
@@ -311,6 +312,24 @@ dg_status degrid_plan_set_compensated(degrid_plan_t p, int enabled)
         p->compensated = enabled;
         p->max_blocks_degrid = 0;               // another kernel instance
     }
+    return DG_OK;
+}
+
+dg_status degrid_plan_set_direct_runs(degrid_plan_t p, int min_runs)
+{
+    if (!p || min_runs < 1 || min_runs > DG_DIRECT_RUNS_NEVER)
+        return DG_ERR_ARG;
+    if ((min_runs < DG_DIRECT_RUNS_NEVER) != (p->direct_runs < DG_DIRECT_RUNS_NEVER))
+        p->max_blocks_degrid = 0;               // another kernel instance
+    p->direct_runs = min_runs;
+    return DG_OK;
+}
+
+dg_status degrid_plan_get_direct_runs(degrid_plan_t p, int *min_runs)
+{
+    if (!p || !min_runs)
+        return DG_ERR_ARG;
+    *min_runs = p->direct_runs;
     return DG_OK;
 }
 

@@ -61,24 +61,47 @@ struct alignas(128) WarpSmem {
 // M[2j + i][a] for i = 0, 1 and a = 0..7 of footprint `key` (subgrid at
 // `base`) with w row gw: lane (a = lane & 7, b = lane >> 3 and b + 4)
 // computes two entries into shared memory, then every lane reads its rows.
+// sum_c g_w[c] s[e + c] for one footprint point (the entries of M; the
+// direct arm forms them the same way, so both arms round alike).
+// With `vec` (16-byte aligned subgrids, nz a multiple of the elements per
+// 16 bytes, and a footprint start z0 that is one too) the four elements are
+// read with 16-byte loads.
+template <int DT>
+__device__ __forceinline__ float2 footprint_point(const void *sub, int64_t e, const float4 &gw, bool vec)
+{
+    float2 s[4];
+    if (vec) {
+        Storage<DT>::load4(sub, e, s);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            s[c] = Storage<DT>::load(sub, e + c);
+    }
+    float2 m;
+    m.x = fmaf(s[3].x, gw.w, fmaf(s[2].x, gw.z, fmaf(s[1].x, gw.y, s[0].x * gw.x)));
+    m.y = fmaf(s[3].y, gw.w, fmaf(s[2].y, gw.z, fmaf(s[1].y, gw.y, s[0].y * gw.x)));
+    return m;
+}
+
+// Whether the footprint starting at `key` can use 16-byte loads.
+template <int DT>
+__device__ __forceinline__ bool vec_footprint(bool vec_ok, int key)
+{
+    return vec_ok && (key % Storage<DT>::kQuad) == 0;
+}
+
 template <int DT>
 __device__ __forceinline__ void build_rows(float2 (&M)[2][8], float2 (&mbuf)[8][8], const void *sub,
                                            int64_t base, int key, const float4 &gw, const Geometry &g,
-                                           int lane, int j)
+                                           bool vec_ok, int lane, int j)
 {
     const int a = lane & 7, b = lane >> 3;
     const int64_t col = base + key + (int64_t)a * g.nz;
+    const bool vec = vec_footprint<DT>(vec_ok, key);
     __syncwarp();                               // previous read-back done
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int64_t e = col + (int64_t)(b + 4 * k) * g.row_stride;
-        const float2 s0 = Storage<DT>::load(sub, e), s1 = Storage<DT>::load(sub, e + 1);
-        const float2 s2 = Storage<DT>::load(sub, e + 2), s3 = Storage<DT>::load(sub, e + 3);
-        float2 m;
-        m.x = fmaf(s3.x, gw.w, fmaf(s2.x, gw.z, fmaf(s1.x, gw.y, s0.x * gw.x)));
-        m.y = fmaf(s3.y, gw.w, fmaf(s2.y, gw.z, fmaf(s1.y, gw.y, s0.y * gw.x)));
-        mbuf[b + 4 * k][a] = m;
-    }
+    for (int k = 0; k < 2; ++k)
+        mbuf[b + 4 * k][a] = footprint_point<DT>(sub, col + (int64_t)(b + 4 * k) * g.row_stride, gw, vec);
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -110,6 +133,36 @@ __device__ __forceinline__ float2 quarter_sum(const float2 (&M)[2][8], const Row
     return __ffma2_rn(t1, make_float2(v.y, v.y), __fmul2_rn(t0, make_float2(v.x, v.x)));
 }
 
+// Direct arm: this lane's quarter of visibility r (footprint `key`, w row gw)
+// from the subgrid itself, M's two rows formed on the fly; the same
+// operations in the same order as build_rows followed by quarter_sum.
+template <int DT>
+__device__ __forceinline__ float2 quarter_sum_direct(const void *sub, int64_t base, int key,
+                                                    const float4 &gw, const RowStage &S, int r, int j,
+                                                    const Geometry &g, bool vec_ok)
+{
+    const bool vec = vec_footprint<DT>(vec_ok, key);
+    const float4 u0 = S.u[r][row_half(r, 0)];
+    const float4 u1 = S.u[r][row_half(r, 1)];
+    const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
+    const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const int64_t e0 = base + key + (int64_t)(2 * j) * g.row_stride, e1 = e0 + g.row_stride;
+    float2 m0[8], m1[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {             // all loads issued before the sums
+        m0[a] = footprint_point<DT>(sub, e0 + (int64_t)a * g.nz, gw, vec);
+        m1[a] = footprint_point<DT>(sub, e1 + (int64_t)a * g.nz, gw, vec);
+    }
+    float2 t0 = __fmul2_rn(m0[0], make_float2(gu[0], gu[0]));
+    float2 t1 = __fmul2_rn(m1[0], make_float2(gu[0], gu[0]));
+#pragma unroll
+    for (int a = 1; a < 8; ++a) {
+        t0 = __ffma2_rn(m0[a], make_float2(gu[a], gu[a]), t0);
+        t1 = __ffma2_rn(m1[a], make_float2(gu[a], gu[a]), t1);
+    }
+    return __ffma2_rn(t1, make_float2(v.y, v.y), __fmul2_rn(t0, make_float2(v.x, v.x)));
+}
+
 // Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
 __device__ __forceinline__ float two_sum(float a, float b, float &e)
 {
@@ -128,24 +181,50 @@ struct MState {
 
 // Sums one half batch (32 visibilities, stage S, issued info I), reduces the
 // four lane partials and stores visibility `lane` of the half.
-template <int DT, bool COMP>
+template <int DT, bool COMP, bool DIRECT>
 __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStage &S, const Issued &I,
                                          const Batch &h, const void *__restrict__ subgrids, int64_t base,
                                          float sc, const Geometry &g, const float4 *wtab,
                                          const float *__restrict__ gwt, float2 *__restrict__ vis_out,
-                                         int lane, int p, int j)
+                                         int direct_runs, bool vec_ok, int lane, int p, int j)
 {
     float2 P[4];                        // pass k: this lane's quarter of visibility 8 (k ^ j) + p
     if (I.uniform) {
         if (I.key0 != ms.key || I.fw0 != ms.fw) {
             const float4 gw = wtab ? wtab[I.fw0] : __ldg(reinterpret_cast<const float4 *>(gwt) + I.fw0);
-            build_rows<DT>(ms.M, ws.m, subgrids, base, I.key0, gw, g, lane, j);
+            build_rows<DT>(ms.M, ws.m, subgrids, base, I.key0, gw, g, vec_ok, lane, j);
             ms.key = I.key0;
             ms.fw = I.fw0;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             P[k] = quarter_sum(ms.M, S, 8 * (k ^ j) + p, j);
+    } else if (DIRECT && I.runs >= direct_runs) {
+        // Short runs: every visibility is summed from its own footprint
+        // (pass k covers visibilities 8k .. 8k + 7; invalid ones stay zero).
+        // Pays off when the footprints of a half overlap (slowly moving
+        // lists whose w row changes often: the other visibilities keep them
+        // in L1); for footprints scattered over the subgrid the cooperative
+        // M builds below read it in longer contiguous pieces and win.  A
+        // separate kernel instance, so the register budget of the plain
+        // path is untouched.
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * k + p;
+            const int kr = __shfl_sync(kFull, I.key, r);
+            const int fr = __shfl_sync(kFull, I.fw, r);
+            float2 acc = make_float2(0.f, 0.f);
+            if (kr >= 0) {
+                const float4 gw = wtab ? wtab[fr] : __ldg(reinterpret_cast<const float4 *>(gwt) + fr);
+                acc = quarter_sum_direct<DT>(subgrids, base, kr, gw, S, r, j, g, vec_ok);
+            }
+            ws.part[k][lane] = acc;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            P[k] = ws.part[k ^ j][lane];
+        __syncwarp();
     } else {
         // Pass k covers visibilities 8k .. 8k + 7 here, so a change of
         // footprint inside a run of the list touches one pass.  Each pass is
@@ -170,7 +249,7 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
                 const int lf = __shfl_sync(kFull, fr, leader);
                 if (lk != ms.key || lf != ms.fw) {
                     const float4 gw = wtab ? wtab[lf] : __ldg(reinterpret_cast<const float4 *>(gwt) + lf);
-                    build_rows<DT>(ms.M, ws.m, subgrids, base, lk, gw, g, lane, j);
+                    build_rows<DT>(ms.M, ws.m, subgrids, base, lk, gw, g, vec_ok, lane, j);
                     ms.key = lk;
                     ms.fw = lf;
                 }
@@ -219,12 +298,12 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
         vis_out[h.b0 + lane] = V;
 }
 
-template <int DT, bool COMP>
+template <int DT, bool COMP, bool DIRECT>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_DEGRID_MIN_BLOCKS)
 degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *__restrict__ scale,
               const double *__restrict__ uvw, const float *__restrict__ guv,
               const float *__restrict__ gwt, const Schedule sched, float2 *__restrict__ vis_out,
-              DeviceStatus *__restrict__ status)
+              DeviceStatus *__restrict__ status, const int direct_runs, const bool vec_ok)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // [w table (optional)] [one WarpSmem per warp]
@@ -283,11 +362,11 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
             if (DT != DG_C64)
                 sc = __ldg(scale + bA.s);
         }
-        sum_half<DT, COMP>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g, wtab, gwt,
-                           vis_out, lane, p, j);
+        sum_half<DT, COMP, DIRECT>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g, wtab, gwt,
+                           vis_out, direct_runs, vec_ok, lane, p, j);
         if (bA.n > kBatch)
-            sum_half<DT, COMP>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc, g, wtab,
-                               gwt, vis_out, lane, p, j);
+            sum_half<DT, COMP, DIRECT>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc, g, wtab,
+                               gwt, vis_out, direct_runs, vec_ok, lane, p, j);
         __syncwarp();
         stage ^= 1;
     }
@@ -298,30 +377,34 @@ size_t smem_bytes(const degrid_plan *p, int warps)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)warps;
 }
 
-template <int DT, bool COMP>
+template <int DT, bool COMP, bool DIRECT>
 cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                    const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP>,
+    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    degrid_kernel<DT, COMP><<<grid_blocks, threads, smem, st>>>(p->geo, subgrids, scale, uvw, p->guv,
-                                                                 p->gw, sched, out, p->status);
+    // 16-byte footprint loads need an aligned stack and nz a multiple of the
+    // elements per 16 bytes
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(subgrids) & 15) == 0 &&
+                        p->geo.nz % Storage<DT>::kQuad == 0;
+    degrid_kernel<DT, COMP, DIRECT><<<grid_blocks, threads, smem, st>>>(
+        p->geo, subgrids, scale, uvw, p->guv, p->gw, sched, out, p->status, p->direct_runs, vec_ok);
     return cudaGetLastError();
 }
 
-template <int DT, bool COMP>
+template <int DT, bool COMP, bool DIRECT>
 int max_blocks(degrid_plan *p)
 {
     int n = 0;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP, DIRECT>,
                                                       p->warps_per_block * kWarp, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
@@ -331,14 +414,21 @@ template <int DT>
 cudaError_t launch_dt(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                       const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
-    return p->compensated ? launch<DT, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
-                          : launch<DT, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+    const bool direct = p->direct_runs < DG_DIRECT_RUNS_NEVER;
+    if (p->compensated)
+        return direct ? launch<DT, true, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
+                      : launch<DT, true, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+    return direct ? launch<DT, false, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
+                  : launch<DT, false, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
 }
 
 template <int DT>
 int max_blocks_dt(degrid_plan *p)
 {
-    return p->compensated ? max_blocks<DT, true>(p) : max_blocks<DT, false>(p);
+    const bool direct = p->direct_runs < DG_DIRECT_RUNS_NEVER;
+    if (p->compensated)
+        return direct ? max_blocks<DT, true, true>(p) : max_blocks<DT, true, false>(p);
+    return direct ? max_blocks<DT, false, true>(p) : max_blocks<DT, false, false>(p);
 }
 
 }  // namespace

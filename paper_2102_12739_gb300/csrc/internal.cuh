@@ -91,30 +91,67 @@ __device__ __forceinline__ bool visibility_coords(double u, double v, double w,
 // ---------------------------------------------------------------------------
 template <int DT> struct Storage;
 
+// load4(base, i): elements i .. i + 3 with 16-byte loads; i must be a
+// multiple of kQuad and the base 16-byte aligned (the launcher checks both
+// and passes the result to the kernels).
 template <> struct Storage<DG_C64> {
     static constexpr int kBytes = 8;
+    static constexpr int kQuad = 2;     // elements per 16 bytes
     __device__ __forceinline__ static float2 load(const void *base, int64_t i)
     {
         return __ldg(reinterpret_cast<const float2 *>(base) + i);
+    }
+    __device__ __forceinline__ static void load4(const void *base, int64_t i, float2 (&s)[4])
+    {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(base) + (i >> 1));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(base) + (i >> 1) + 1);
+        s[0] = make_float2(a.x, a.y);
+        s[1] = make_float2(a.z, a.w);
+        s[2] = make_float2(b.x, b.y);
+        s[3] = make_float2(b.z, b.w);
     }
 };
 
 template <> struct Storage<DG_C32_F16> {
     static constexpr int kBytes = 4;
-    __device__ __forceinline__ static float2 load(const void *base, int64_t i)
+    static constexpr int kQuad = 4;
+    __device__ __forceinline__ static float2 cvt(unsigned u)
     {
-        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(base) + i);
         __half2 h = *reinterpret_cast<const __half2 *>(&u);
         return __half22float2(h);
+    }
+    __device__ __forceinline__ static float2 load(const void *base, int64_t i)
+    {
+        return cvt(__ldg(reinterpret_cast<const unsigned *>(base) + i));
+    }
+    __device__ __forceinline__ static void load4(const void *base, int64_t i, float2 (&s)[4])
+    {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + (i >> 2));
+        s[0] = cvt(q.x);
+        s[1] = cvt(q.y);
+        s[2] = cvt(q.z);
+        s[3] = cvt(q.w);
     }
 };
 
 template <> struct Storage<DG_C32_BF16> {
     static constexpr int kBytes = 4;
+    static constexpr int kQuad = 4;
+    __device__ __forceinline__ static float2 cvt(unsigned u)
+    {
+        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+    }
     __device__ __forceinline__ static float2 load(const void *base, int64_t i)
     {
-        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(base) + i);
-        return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+        return cvt(__ldg(reinterpret_cast<const unsigned *>(base) + i));
+    }
+    __device__ __forceinline__ static void load4(const void *base, int64_t i, float2 (&s)[4])
+    {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + (i >> 2));
+        s[0] = cvt(q.x);
+        s[1] = cvt(q.y);
+        s[2] = cvt(q.z);
+        s[3] = cvt(q.w);
     }
 };
 
@@ -173,6 +210,7 @@ struct degrid_plan {
     int warps_per_block;
     int blocks_per_sm;
     int compensated;            // compensated (TwoSum) reduction of the lane partials
+    int direct_runs;            // non-uniform halves with at least this many runs take the direct sum
     int max_blocks_degrid;      // occupancy results, 0 = not computed yet
     int max_blocks_adjoint;
     int n_slots;                // timing event pairs (0 = timing off)

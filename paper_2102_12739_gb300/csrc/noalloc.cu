@@ -143,6 +143,7 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
     p.chunk = kChunk;
     p.warps_per_block = dg_max_warps_per_block();
     p.blocks_per_sm = 0;
+    p.direct_runs = DG_DIRECT_RUNS_DEFAULT;
 
     cudaStream_t s = (cudaStream_t)stream;
     // The array keeps whatever the previous call left: the status words must

@@ -187,11 +187,13 @@ __device__ __forceinline__ int row_half(int r, int h) { return RowStage::slot(r,
 
 // What issue_rows leaves in registers for the summing step: this lane's
 // visibility's footprint key (-1 when invalid or past the batch) and w row,
-// and whether the whole batch shares lane 0's key and row.
+// whether the whole batch shares lane 0's key and row, and otherwise how
+// many runs of equal key and row it holds.
 struct Issued {
     int key, fw;
     int key0, fw0;
     bool uniform;
+    int runs;           // runs of equal (key, w row) among the valid visibilities (1 if uniform)
 };
 
 // Stage 2 of a degridding batch: snap, and copy the g_u / g_v rows into the
@@ -212,6 +214,11 @@ __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, c
     r.fw0 = __shfl_sync(kFull, r.fw, 0);
     // lanes past the end of the batch compute values nobody stores
     r.uniform = __all_sync(kFull, !in || (r.key == r.key0 && r.fw == r.fw0)) && r.key0 >= 0;
+    r.runs = 1;
+    if (!r.uniform) {
+        const int kp = __shfl_up_sync(kFull, r.key, 1), fp = __shfl_up_sync(kFull, r.fw, 1);
+        r.runs = __popc(__ballot_sync(kFull, r.key >= 0 && (lane == 0 || r.key != kp || r.fw != fp)));
+    }
     const unsigned bad = __ballot_sync(kFull, in && !valid);
     if (lane == 0 && bad)
         atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));

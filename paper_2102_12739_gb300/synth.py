@@ -193,6 +193,16 @@ def piecewise_list(n: int, rng, shape=SUBGRID_SHAPE) -> np.ndarray:
     return np.concatenate(pieces, axis=0) if pieces else np.zeros((0, 3))
 
 
+def scattered_list(n: int, rng, shape=SUBGRID_SHAPE) -> np.ndarray:
+    """n points uniform in the valid box: no two consecutive visibilities
+    share a footprint (sparse uv coverage)."""
+    ny, nx, _ = shape
+    ulo, uhi = uv_box(nx)
+    vlo, vhi = uv_box(ny)
+    return np.stack([rng.uniform(ulo, uhi, n), rng.uniform(vlo, vhi, n),
+                     rng.uniform(W_LO, W_HI, n)], axis=1)
+
+
 def offsets_from_counts(counts) -> np.ndarray:
     counts = np.asarray(counts, dtype=np.int64)
     out = np.zeros(len(counts) + 1, dtype=np.int64)
@@ -263,6 +273,15 @@ def lines_workload(name: str, counts, shape=SUBGRID_SHAPE, ids=None) -> Workload
                     None if ids is None else np.asarray(gid, dtype=np.int64))
 
 
+def scattered_workload(name: str, counts, shape=SUBGRID_SHAPE) -> Workload:
+    """Every subgrid's list is scattered uniformly over the valid box."""
+    counts = [int(c) for c in counts]
+    parts = [scattered_list(c, np.random.default_rng([SEED_UVW, s]), shape)
+             for s, c in enumerate(counts)]
+    uvw = np.ascontiguousarray(np.concatenate(parts, axis=0)) if parts else np.zeros((0, 3))
+    return Workload(name, len(counts), tuple(shape), uvw, offsets_from_counts(counts))
+
+
 def batched_counts(n_subgrids: int, lo: float = 1e3, hi: float = 1e6) -> np.ndarray:
     """Visibility counts log-uniform in [lo, hi], rounded to integers."""
     rng = np.random.default_rng(SEED_STRUCTURE)
@@ -289,6 +308,8 @@ def workload(name: str) -> Workload:
     lines16_250k   its first 16 subgrids (4M visibilities; profiling case)
     batched512     512 subgrids, log-uniform counts in [1e3, 1e6]
     diff32_100k    32 subgrids, 100,000 visibilities each (adjoint)
+    scatter16_250k 16 subgrids, 250,000 scattered visibilities each (4M; no
+                   footprint shared by consecutive visibilities)
     """
     if name == "line1_20k":
         return lines_workload(name, [20_000])
@@ -300,4 +321,6 @@ def workload(name: str) -> Workload:
         return batched_workload(name, 512)
     if name == "diff32_100k":
         return lines_workload(name, [100_000] * 32)
+    if name == "scatter16_250k":
+        return scattered_workload(name, [250_000] * 16)
     raise KeyError(name)

@@ -2,10 +2,13 @@
 
 The paper picks N_b, the visibilities per thread block, by hand and finds
 that the best value depends on the step du, dv, dw while N_b = 32 is good
-enough (Section "Results").  Here the equivalent knobs are the chunk size
-(visibilities per work item), warps per CTA and resident CTAs per SM; this
-module times a small grid of candidates on the caller's own inputs with CUDA
-events and keeps the fastest on the plan.  Results are cached in a JSON file
+enough, and it switches between kernel variants by list length (Section
+"Results").  Here the knobs are the chunk size (visibilities per work item),
+warps per CTA, resident CTAs per SM and the summing arm (footprint cache only,
+or the direct per-visibility arm for halves with many short runs, which wins
+when footprints overlap but their w rows change often); this module times a
+small grid of candidates on the caller's own inputs with CUDA events and
+keeps the fastest on the plan.  Results are cached in a JSON file
 keyed by GPU name, storage type and a coarse description of the inputs, so a
 later call with similar inputs reuses them without timing.
 
@@ -20,12 +23,22 @@ import math
 import os
 from typing import Iterable, Optional
 
+NEVER = 33          # DG_DIRECT_RUNS_NEVER
+SHORT = 9           # DG_DIRECT_RUNS_SHORT
+
 DEFAULT_CANDIDATES = [
-    (chunk, warps, bps)
-    for chunk in (128, 256, 512, 1024, 2048)
+    (chunk, warps, 0, direct)
+    for chunk in (128, 256, 512, 1024)
     for warps in (4, 8)
-    for bps in (0,)
+    for direct in (NEVER, SHORT)
 ]
+
+_KEYS = ("chunk", "warps_per_block", "blocks_per_sm", "direct_runs")
+
+
+def _apply(plan, t: dict) -> None:
+    plan.set_tuning(t["chunk"], t["warps_per_block"], t["blocks_per_sm"])
+    plan.set_direct_runs(t.get("direct_runs", NEVER))
 
 
 def _cache_path() -> str:
@@ -65,7 +78,8 @@ def cache_key(plan, n_subgrids: int, n_vis: int) -> str:
 
 def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
              candidates: Optional[Iterable] = None, iters: int = 5, use_cache: bool = True):
-    """Time `candidates` (chunk, warps_per_block, blocks_per_sm) and keep the best.
+    """Time `candidates` (chunk, warps_per_block, blocks_per_sm[, direct_runs])
+    and keep the best; a candidate without direct_runs keeps the plan's.
 
     Returns {"tuning": {...}, "ms": best median kernel ms, "timings": [...]}.
     """
@@ -75,9 +89,8 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
     key = cache_key(plan, S, n)
     cache = _load_cache() if use_cache else {}
     if key in cache:
-        t = cache[key]["tuning"]
-        plan.set_tuning(t["chunk"], t["warps_per_block"], t["blocks_per_sm"])
-        return dict(cache[key], cached=True)
+        _apply(plan, cache[key]["tuning"])
+        return dict(cache[key], tuning=plan.tuning(), cached=True)
     if os.environ.get("DEGRID_TUNE", "1") == "0":
         return {"tuning": plan.tuning(), "ms": None, "timings": [], "cached": False}
     cands = list(candidates) if candidates is not None else list(DEFAULT_CANDIDATES)
@@ -85,9 +98,12 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
     plan.enable_timing(max(iters, 1))
     timings = []
     try:
-        for chunk, warps, bps in cands:
+        for cand in cands:
+            chunk, warps, bps = cand[:3]
+            direct = cand[3] if len(cand) > 3 else plan.direct_runs
             try:
-                plan.set_tuning(chunk, warps, bps)
+                _apply(plan, {"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
+                              "direct_runs": direct})
             except Exception:
                 continue
             for _ in range(2):                      # warm-up (also sizes scratch)
@@ -96,15 +112,14 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
                 plan.degrid(subgrids, uvw, vis_offsets, scale=scale, out=out)
             ms = sorted(plan.kernel_times_ms(iters))
             timings.append({"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
-                            "ms": ms[len(ms) // 2]})
+                            "direct_runs": direct, "ms": ms[len(ms) // 2]})
     finally:
         plan.enable_timing(0)
     if not timings:
         raise RuntimeError("autotune: no candidate could be timed")
     best = min(timings, key=lambda t: t["ms"])
-    plan.set_tuning(best["chunk"], best["warps_per_block"], best["blocks_per_sm"])
-    result = {"tuning": {k: best[k] for k in ("chunk", "warps_per_block", "blocks_per_sm")},
-              "ms": best["ms"], "timings": timings}
+    _apply(plan, best)
+    result = {"tuning": {k: best[k] for k in _KEYS}, "ms": best["ms"], "timings": timings}
     if use_cache:
         cache[key] = {"tuning": result["tuning"], "ms": result["ms"]}
         _store_cache(cache)

@@ -73,7 +73,18 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.degrid_coords_execute(None, None, None, 0, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_compensated(None, 1) == _native.DG_ERR_ARG
     assert lib.degrid_plan_get_compensated(None, None) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_set_direct_runs(None, 9) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_get_direct_runs(None, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_tuning(None, 256, 8, 0) == _native.DG_ERR_ARG
     assert lib.degrid_get_status(None, None, None) == _native.DG_ERR_ARG
     assert lib.degrid_pack_subgrids(None, 0, 1, 4, None, None, None) == _native.DG_ERR_DTYPE
     assert lib.degrid_pack_subgrids(None, 1, -1, 4, None, None, None) == _native.DG_ERR_ARG
+
+
+def test_header_constants_match_the_binding():
+    text = open(HEADER).read()
+    for name in ("DG_DIRECT_RUNS_NEVER", "DG_DIRECT_RUNS_SHORT"):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(_native, name)
+    assert re.search(r"#define\s+DG_DIRECT_RUNS_DEFAULT\s+DG_DIRECT_RUNS_NEVER", text)
+    assert _native.DG_DIRECT_RUNS_DEFAULT == _native.DG_DIRECT_RUNS_NEVER

@@ -219,6 +219,31 @@ def test_reduced_precision_storage(dtype):
     assert rel_l2(got, ref_q) <= 2e-6
 
 
+@pytest.mark.parametrize("kind", ["scatter", "mixed", "line"])
+def test_direct_arm_is_bitwise_the_cached_path(kind):
+    # the direct (per-visibility) arm and the footprint-cache arm do the same
+    # arithmetic in the same order: every threshold gives the same bits
+    d = dev()
+    w = small_workload([700, 0, 513, 64], kind=kind, seed=31)
+    w.uvw[9] = [np.nan, 10.0, 1.5]
+    sub_np = synth.subgrid_stack(4)
+    sub, uvw, offs = upload(w, sub_np)
+    outs = {}
+    with dg.DegridPlan(device=d) as p:
+        assert p.direct_runs == dg._native.DG_DIRECT_RUNS_DEFAULT
+        for runs in (1, 2, 9, 33):
+            p.set_direct_runs(runs)
+            outs[runs] = p.degrid(sub, uvw, offs).cpu().numpy()
+            assert p.status() == 1
+        with pytest.raises(dg.DegridError):
+            p.set_direct_runs(0)
+    for runs in (2, 9, 33):
+        np.testing.assert_array_equal(outs[1].view(np.uint32), outs[runs].view(np.uint32))
+    ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert bad == 1 and outs[1][9] == 0
+    assert rel_l2(outs[1], ref) <= TOL["c64"]
+
+
 @pytest.mark.parametrize("dtype", ["c64", "f16", "bf16"])
 def test_compensated_reduction(dtype):
     # the compensated form: same bar as the plain one, deterministic, and no
@@ -432,7 +457,7 @@ def test_autotune_picks_a_candidate_and_caches_it(plan, tmp_path, monkeypatch):
     sub, uvw, offs = upload(w, synth.subgrid_stack(2))
     saved = plan.tuning()
     try:
-        cands = [(128, 4, 0), (256, 8, 0), (512, 8, 1)]
+        cands = [(128, 4, 0), (256, 8, 0, 9), (512, 8, 1)]
         res = dg.autotune(plan, sub, uvw, offs, candidates=cands, iters=2)
         assert not res["cached"] and len(res["timings"]) == 3
         assert plan.tuning() == res["tuning"]
@@ -443,6 +468,7 @@ def test_autotune_picks_a_candidate_and_caches_it(plan, tmp_path, monkeypatch):
         assert rel_l2(plan.degrid(sub, uvw, offs).cpu().numpy(), ref) <= TOL["c64"]
     finally:
         plan.set_tuning(saved["chunk"], saved["warps_per_block"], saved["blocks_per_sm"])
+        plan.set_direct_runs(saved["direct_runs"])
 
 
 def test_adjoint_dense_lines_full_size_sampled(plan):
