@@ -56,6 +56,8 @@ def _load():
             lib.oracle_degrid.restype = _I64
             lib.oracle_degrid.argtypes = ([_I32] * 3 + [_P, _I32, _I32, _P, _I32, _I32,
                                                         _I32, _P, _P, _P, _I64, _P])
+            lib.oracle_degrid_2d.restype = _I64
+            lib.oracle_degrid_2d.argtypes = lib.oracle_degrid.argtypes
             lib.oracle_grid.restype = _I64
             lib.oracle_grid.argtypes = ([_I32] * 3 + [_P, _I32, _I32, _P, _I32, _I32,
                                                       _I32, _P, _P, _I64, _P, _P, _I32])
@@ -131,6 +133,27 @@ def degrid(g_uv, g_w, subgrids, uvw, vis_offsets):
                                 _ptr(uvw), _ptr(offs), uvw.shape[0], _ptr(out))
     if bad < 0:
         raise ValueError("oracle_degrid: invalid vis_offsets")
+    return out[:, 0] + 1j * out[:, 1], int(bad)
+
+
+def degrid_2d(g_uv2, g_w, subgrids, uvw, vis_offsets):
+    """Degridding with a non-separable G_uv table g_uv2 [O][O][W][W] indexed
+    [fv][fu][b][a]; complex128 [n] and the invalid count."""
+    g_uv2 = np.ascontiguousarray(g_uv2, dtype=np.float64)
+    O, O2, W, W2 = g_uv2.shape
+    assert O == O2 and W == W2
+    g_w = np.ascontiguousarray(g_w, dtype=np.float64)
+    sub = _complex_to_pairs(subgrids)
+    S, ny, nx, nz = sub.shape[:4]
+    uvw = _f64(uvw).reshape(-1, 3)
+    offs = np.ascontiguousarray(vis_offsets, dtype=np.int64)
+    assert offs.shape == (S + 1,)
+    out = np.empty((uvw.shape[0], 2), dtype=np.float64)
+    bad = _load().oracle_degrid_2d(nx, ny, nz, _ptr(g_uv2), W, O, _ptr(g_w), g_w.shape[1],
+                                   g_w.shape[0], S, _ptr(sub), _ptr(uvw), _ptr(offs),
+                                   uvw.shape[0], _ptr(out))
+    if bad < 0:
+        raise ValueError("oracle_degrid_2d: invalid vis_offsets")
     return out[:, 0] + 1j * out[:, 1], int(bad)
 
 

@@ -171,6 +171,56 @@ int64_t oracle_degrid(int nx, int ny, int nz,
     return bad;
 }
 
+/* Degridding with a non-separable G_uv.  The paper states G_uv as a kernel of
+ * support 8 x 8 (Section "Implementation"); the separable table above is the
+ * special case G_uv(a, b) = g(a) g(b).  Here the oversampled table holds one
+ * W x W weight block per pair of oversampled offsets:
+ *   vis_out[i] = sum_b sum_a sum_c G[fv][fu][b][a] g_w[fw][c] s[y0+b][x0+a][z0+c]
+ * with g_uv2: double [O][O][W][W] indexed [fv][fu][b][a] (b along v / y, a
+ * along u / x), O = uv_oversample.  Coordinates, validity and the w table are
+ * exactly those of oracle_degrid.  Returns the invalid count, -1 for bad
+ * offsets. */
+int64_t oracle_degrid_2d(int nx, int ny, int nz,
+                         const double *g_uv2, int uv_support, int uv_oversample,
+                         const double *g_w, int w_support, int w_oversample,
+                         int n_subgrids, const double *subgrids,
+                         const double *uvw, const int64_t *vis_offsets,
+                         int64_t n_vis, double *vis_out)
+{
+    if (!offsets_ok(n_subgrids, vis_offsets, n_vis))
+        return -1;
+    const int64_t plane = (int64_t)ny * nx * nz;
+    const int64_t block = (int64_t)uv_support * uv_support;
+    int64_t bad = 0;
+    for (int s = 0; s < n_subgrids; ++s) {
+        const double *sg = subgrids + 2 * plane * s;
+        const int64_t lo = vis_offsets[s], hi = vis_offsets[s + 1];
+#pragma omp parallel for reduction(+ : bad) schedule(static)
+        for (int64_t i = lo; i < hi; ++i) {
+            coords_t c;
+            double re = 0.0, im = 0.0;
+            if (visibility_coords(uvw + 3 * i, nx, ny, nz, uv_support, uv_oversample,
+                                  w_support, w_oversample, &c)) {
+                const double *G = g_uv2 + ((int64_t)c.fv * uv_oversample + c.fu) * block;
+                const double *gw = g_w + c.fw * w_support;
+                for (int b = 0; b < uv_support; ++b)
+                    for (int a = 0; a < uv_support; ++a)
+                        for (int k = 0; k < w_support; ++k) {
+                            double w = G[b * uv_support + a] * gw[k];
+                            int64_t e = ((c.y0 + b) * nx + (c.x0 + a)) * nz + (c.z0 + k);
+                            re += w * sg[2 * e];
+                            im += w * sg[2 * e + 1];
+                        }
+            } else {
+                bad += 1;
+            }
+            vis_out[2 * i] = re;
+            vis_out[2 * i + 1] = im;
+        }
+    }
+    return bad;
+}
+
 /* Adjoint (gridding): grid_out[s][y0+b][x0+a][z0+c] += weight * vis_in[i],
  * the transpose of oracle_degrid (real weights, so no conjugation).
  * grid_out: double [S][ny][nx][nz][2], zeroed first unless accumulate.

@@ -304,3 +304,97 @@ def test_quantize_scale_and_range():
         err = np.abs(deq - sub) / np.repeat(np.maximum(scale, 1e-30), 256).reshape(sub.shape)
         tol = 2 ** -11 if dt == "f16" else 2 ** -8
         assert err[:2].max() <= tol * np.sqrt(2)
+
+
+# ---------------------------------------------------------------------------
+# Non-separable G_uv (oracle.degrid_2d): G[fv][fu][b][a], oversampling 64
+# ---------------------------------------------------------------------------
+
+O2D = 64
+
+
+def _onehot_positions(O):
+    fv, fu = np.meshgrid(np.arange(O), np.arange(O), indexing="ij")
+    return (3 * fv + fu) % 8, (5 * fu + 2 * fv + 1) % 8      # (b*, a*) per (fv, fu)
+
+
+def test_2d_one_hot_blocks_pin_orientation():
+    # Every (fv, fu) block has its single 1 at a different (b*, a*) that is
+    # not symmetric in fv/fu or in b/a, so swapping the offsets, the block's
+    # axes or the start offset picks the wrong sample.
+    shape = (40, 56, 4)
+    bstar, astar = _onehot_positions(O2D)
+    G = np.zeros((O2D, O2D, 8, 8))
+    fv_i, fu_i = np.meshgrid(np.arange(O2D), np.arange(O2D), indexing="ij")
+    G[fv_i, fu_i, bstar, astar] = 1.0
+    g_w = np.zeros_like(G_W)
+    g_w[77, 2] = 1.0
+    rng = np.random.default_rng(41)
+    sub = random_subgrids(rng, 1, shape)
+    n = 500
+    iu = rng.integers(3, shape[1] - 4, n)
+    iv = rng.integers(3, shape[0] - 4, n)
+    fu = rng.integers(0, O2D, n)
+    fv = rng.integers(0, O2D, n)
+    uvw = np.stack([iu + fu / O2D, iv + fv / O2D, np.full(n, 1.0 + 77 / 128.0)], axis=1)
+    vis, bad = oracle.degrid_2d(G, g_w, sub, uvw, [0, n])
+    assert bad == 0
+    expect = sub[0, iv - 3 + bstar[fv, fu], iu - 3 + astar[fv, fu], 2]
+    np.testing.assert_array_equal(vis, expect)
+
+
+def test_2d_separable_table_matches_separable_oracle():
+    # G[fv][fu][b][a] = g[fv][b] g[fu][a] is the separable method: the two
+    # oracles agree to FP64 rounding (the weight products round differently)
+    g = synth.gcf_table(8, O2D, 2.3 * 8)
+    G = g[:, None, :, None] * g[None, :, None, :]
+    rng = np.random.default_rng(42)
+    shape = (48, 40, 4)
+    sub = random_subgrids(rng, 2, shape)
+    parts = [synth.random_line(300, np.random.default_rng([42, s]), shape) for s in range(2)]
+    uvw = np.concatenate(parts)
+    sep, bad1 = oracle.degrid(g, G_W, sub, uvw, [0, 300, 600])
+    two, bad2 = oracle.degrid_2d(G, G_W, sub, uvw, [0, 300, 600])
+    assert bad1 == bad2 == 0
+    assert np.max(np.abs(two - sep)) <= 1e-13 * np.max(np.abs(sep))
+
+
+def test_2d_diagonal_kernel_closed_form():
+    # G = identity block for every offset pair: a non-separable kernel whose
+    # degridded value is the sum of the samples on the footprint's diagonal
+    # y0 + b, x0 + b (times the w weights)
+    shape = (32, 32, 4)
+    G = np.broadcast_to(np.eye(8), (O2D, O2D, 8, 8)).copy()
+    rng = np.random.default_rng(43)
+    sub = random_subgrids(rng, 1, shape)
+    n = 300
+    iu = rng.integers(3, shape[1] - 4, n)
+    iv = rng.integers(3, shape[0] - 4, n)
+    fw = rng.integers(0, 128, n)
+    uvw = np.stack([iu + rng.integers(0, O2D, n) / O2D, iv + rng.integers(0, O2D, n) / O2D,
+                    1.0 + fw / 128.0], axis=1)
+    vis, bad = oracle.degrid_2d(G, G_W, sub, uvw, [0, n])
+    assert bad == 0
+    b = np.arange(8)
+    diag = sub[0][(iv - 3)[:, None] + b, (iu - 3)[:, None] + b]      # [n][8][nz]
+    expect = np.einsum("nbc,nc->n", diag[:, :, :4], G_W[fw])
+    np.testing.assert_allclose(vis, expect, rtol=1e-13, atol=1e-13)
+
+
+def test_2d_constant_subgrid_is_block_sum():
+    shape = (24, 24, 4)
+    c = -0.5 + 2.0j
+    sub = np.full((1,) + shape, c)
+    rng = np.random.default_rng(44)
+    G = rng.standard_normal((O2D, O2D, 8, 8))
+    n = 300
+    fu, fv, fw = rng.integers(0, O2D, n), rng.integers(0, O2D, n), rng.integers(0, 128, n)
+    iu = rng.integers(3, shape[1] - 4, n)
+    iv = rng.integers(3, shape[0] - 4, n)
+    uvw = np.stack([iu + fu / O2D, iv + fv / O2D, 1.0 + fw / 128.0], axis=1)
+    uvw[7] = [np.nan, 5.0, 1.5]
+    vis, bad = oracle.degrid_2d(G, G_W, sub, uvw, [0, n])
+    assert bad == 1 and vis[7] == 0
+    expect = c * G[fv, fu].sum(axis=(1, 2)) * G_W[fw].sum(1)
+    expect[7] = 0
+    np.testing.assert_allclose(vis, expect, rtol=1e-12, atol=1e-12)
