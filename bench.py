@@ -70,6 +70,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-scatter", action="store_true")
+    ap.add_argument("--no-table2d", action="store_true")
     ap.add_argument("--aux-steps", type=int, default=50,
                     help="timed steps of the batched and adjoint sections")
     return ap.parse_args()
@@ -333,6 +334,38 @@ def scatter_section(torch, dg, synth, dev, flush, steps):
                         "consecutive visibilities)", "unit": UNIT, "steps": steps, "by_storage": res}
 
 
+def table2d_section(torch, dg, synth, dev, flush, steps, sub, sub_np, uvw, offs, w):
+    """The headline workload with a non-separable G_uv: a circular
+    Kaiser-Bessel table [64][64][8][8] (weights read per visibility from L2)."""
+    import oracle
+    G2 = synth.default_table_2d()
+    out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    with dg.DegridPlan(device=dev, g_uv2=G2) as plan:
+        plan.enable_timing(steps)
+
+        def step():
+            plan.degrid(sub, uvw, offs, out=out)
+        warm_up(torch, step, flush, 3, min_seconds=0.3)
+        s_ms, k_ms = time_steps(torch, plan, step, steps, flush, torch.cuda.current_stream(dev))
+        assert plan.status() == 0
+    got = out.cpu().numpy()
+    rng = np.random.default_rng(0)
+    subs = np.linspace(0, w.n_subgrids - 1, 4).astype(int)
+    idx = np.concatenate([np.unique(rng.integers(w.vis_offsets[s], w.vis_offsets[s + 1], 2000))
+                          for s in subs])
+    counts = [np.count_nonzero((idx >= w.vis_offsets[s]) & (idx < w.vis_offsets[s + 1])) for s in subs]
+    _, g_w = synth.default_tables()
+    ref, _ = oracle.degrid_2d(G2, g_w, np.stack([sub_np[s] for s in subs]).astype(np.complex128),
+                              w.uvw[idx], np.concatenate([[0], np.cumsum(counts)]))
+    ms = sorted(s_ms)[len(s_ms) // 2]
+    return {"workload": WORKLOAD + " with a non-separable G_uv: circular Kaiser-Bessel table, "
+                        "oversampling 64 ([64][64][8][8] FP32, 1 MiB)",
+            "value": w.n_vis / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "kernel_ms": sorted(k_ms)[len(k_ms) // 2],
+            "rel_l2_vs_oracle": float(np.linalg.norm(got[idx] - ref) / np.linalg.norm(ref)),
+            "steps": steps}
+
+
 def adjoint_section(torch, dg, synth, dev, flush, steps):
     """Gridding (the adjoint) of 32 subgrids x 100,000 random-line visibilities."""
     w = synth.workload("diff32_100k")
@@ -550,6 +583,10 @@ def run_ours(args, rank, world):
 
     if not args.no_adjoint:
         line["adjoint"] = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)
+
+    if not args.no_table2d:
+        line["table2d"] = table2d_section(torch, dg, synth, dev, flush, args.aux_steps, sub, sub_np,
+                                          uvw, offs, w)
 
     if not args.no_scatter:
         line["scatter"] = scatter_section(torch, dg, synth, dev, flush, args.aux_steps)

@@ -101,6 +101,26 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz,
 
 /* Release the plan and every device buffer it owns.  Synchronises the
  * plan's device first.  NULL is ignored. */
+/*
+ * Create a plan with a non-separable G_uv (the paper states G_uv as a kernel
+ * of support 8 x 8, Section "Implementation"; degrid_plan_create takes the
+ * separable special case g(a) g(b) at high oversampling).
+ *   g_uv2          HOST double [uv_oversample][uv_oversample][8][8], indexed
+ *                  [fv][fu][b][a]: block (fv, fu) holds the weight of
+ *                  footprint point (row b along v, column a along u) for
+ *                  oversampled offsets fv and fu; copied (rounded to FP32)
+ *   uv_oversample  power of two, 1 .. DG_TABLE2D_MAX_OVERSAMPLE (the FP32
+ *                  table, uv_oversample^2 * 256 bytes, stays L2-resident)
+ * and the other arguments as for degrid_plan_create (support 8 implied).
+ * degrid_execute (all storage types, compensated or not) uses the 2D table;
+ * grid_adjoint_execute returns DG_ERR_UNSUPPORTED for such a plan and the
+ * direct summing arm is not used.
+ */
+#define DG_TABLE2D_MAX_OVERSAMPLE 256
+dg_status degrid_plan_create_2d(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv2,
+                                int uv_oversample, const double *g_w, int w_support,
+                                int w_oversample, dg_dtype dtype, int device);
+
 void degrid_plan_destroy(degrid_plan_t plan);
 
 /*
@@ -211,7 +231,8 @@ dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
  * (real weights, so the adjoint needs no conjugation).  sub_out is complex64
  * [S][ny][nx][nz] on the DEVICE, zeroed first unless accumulate != 0.
  * FP32 atomic accumulation: the summation order, and so the last bits, are
- * not deterministic.  Other arguments as for degrid_execute.
+ * not deterministic.  Other arguments as for degrid_execute.  A plan made by
+ * degrid_plan_create_2d gives DG_ERR_UNSUPPORTED.
  */
 dg_status grid_adjoint_execute(degrid_plan_t plan, void *stream, int n_subgrids,
                                const double *uvw, const int64_t *vis_offsets,

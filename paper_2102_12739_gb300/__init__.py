@@ -74,7 +74,7 @@ class DegridPlan:
     """
 
     def __init__(self, shape=synth.SUBGRID_SHAPE, g_uv=None, g_w=None, dtype: str = "c64",
-                 device=None, compensated: bool = False):
+                 device=None, compensated: bool = False, g_uv2=None):
         torch = _torch()
         lib = load()
         if dtype not in DTYPES:
@@ -97,12 +97,27 @@ class DegridPlan:
         self.dtype = dtype
         ny, nx, nz = self.shape
         h = ctypes.c_void_p()
-        st = lib.degrid_plan_create(ctypes.byref(h), nx, ny, nz,
-                                    self.g_uv.ctypes.data_as(ctypes.c_void_p), self.g_uv.shape[1],
-                                    self.g_uv.shape[0], self.g_w.ctypes.data_as(ctypes.c_void_p),
-                                    self.g_w.shape[1], self.g_w.shape[0], DTYPES[dtype],
-                                    device.index)
-        check(st, "degrid_plan_create")
+        self.table2d = g_uv2 is not None
+        if self.table2d:
+            # non-separable G_uv [O][O][8][8] indexed [fv][fu][b][a]
+            self.g_uv2 = np.ascontiguousarray(g_uv2, dtype=np.float64)
+            O = self.g_uv2.shape[0]
+            if self.g_uv2.shape != (O, O, 8, 8):
+                raise ValueError("g_uv2 must have shape [O][O][8][8]")
+            st = lib.degrid_plan_create_2d(ctypes.byref(h), nx, ny, nz,
+                                           self.g_uv2.ctypes.data_as(ctypes.c_void_p), O,
+                                           self.g_w.ctypes.data_as(ctypes.c_void_p),
+                                           self.g_w.shape[1], self.g_w.shape[0], DTYPES[dtype],
+                                           device.index)
+            check(st, "degrid_plan_create_2d")
+        else:
+            st = lib.degrid_plan_create(ctypes.byref(h), nx, ny, nz,
+                                        self.g_uv.ctypes.data_as(ctypes.c_void_p),
+                                        self.g_uv.shape[1], self.g_uv.shape[0],
+                                        self.g_w.ctypes.data_as(ctypes.c_void_p),
+                                        self.g_w.shape[1], self.g_w.shape[0], DTYPES[dtype],
+                                        device.index)
+            check(st, "degrid_plan_create")
         self._h = h
         if compensated:
             self.set_compensated(True)

@@ -26,6 +26,7 @@ DG_C64 = 0
 DG_C32_F16 = 1
 DG_C32_BF16 = 2
 
+DG_TABLE2D_MAX_OVERSAMPLE = 256
 DG_DIRECT_RUNS_NEVER = 33
 DG_DIRECT_RUNS_DEFAULT = DG_DIRECT_RUNS_NEVER
 DG_DIRECT_RUNS_SHORT = 9
@@ -41,6 +42,7 @@ SIGNATURES = {
     "degrid_plan_destroy": (None, [_P]),
     "degrid_plan_set_tuning": (_I, [_P, _I, _I, _I]),
     "degrid_plan_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "degrid_plan_create_2d": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P, _I, _P, _I, _I, _I, _I]),
     "degrid_plan_set_compensated": (_I, [_P, _I]),
     "degrid_plan_set_direct_runs": (_I, [_P, _I]),
     "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),

@@ -79,6 +79,7 @@ void free_plan_buffers(degrid_plan *p)
 {
     free_events(p);
     cudaFree(p->guv);
+    cudaFree(p->guv2);
     cudaFree(p->gw);
     cudaFree(p->status);
     cudaFree(p->work_counter);
@@ -177,14 +178,18 @@ const char *degrid_status_string(dg_status status)
 
 const char *degrid_version(void) { return "gb300-degrid 0.1 (sm_103a)"; }
 
-dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv,
-                             int uv_support, int uv_oversample, const double *g_w,
-                             int w_support, int w_oversample, dg_dtype dtype, int device)
+// Plan creation for either a separable G_uv table g_uv [O][8] or a 2D one
+// g_uv2 [O][O][8][8] (exactly one of them non-null).
+static dg_status plan_create(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv,
+                      const double *g_uv2, int uv_support, int uv_oversample, const double *g_w,
+                      int w_support, int w_oversample, dg_dtype dtype, int device)
 {
     if (!out)
         return DG_ERR_ARG;
     *out = nullptr;
-    if (!g_uv || !g_w || nx <= 0 || ny <= 0 || nz <= 0 || device < 0)
+    if ((!g_uv && !g_uv2) || !g_w || nx <= 0 || ny <= 0 || nz <= 0 || device < 0)
+        return DG_ERR_ARG;
+    if (g_uv2 && (uv_oversample < 1 || uv_oversample > DG_TABLE2D_MAX_OVERSAMPLE))
         return DG_ERR_ARG;
     if (dtype != DG_C64 && dtype != DG_C32_F16 && dtype != DG_C32_BF16)
         return DG_ERR_DTYPE;
@@ -235,12 +240,16 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     p->direct_runs = DG_DIRECT_RUNS_DEFAULT;
 
     dg_status st = DG_OK;
-    std::vector<float> h_uv((size_t)uv_oversample * uv_support), h_w((size_t)w_oversample * w_support);
+    const size_t n_uv = g_uv2 ? (size_t)uv_oversample * uv_oversample * uv_support * uv_support
+                              : (size_t)uv_oversample * uv_support;
+    const double *src_uv = g_uv2 ? g_uv2 : g_uv;
+    std::vector<float> h_uv(n_uv), h_w((size_t)w_oversample * w_support);
     for (size_t i = 0; i < h_uv.size(); ++i)
-        h_uv[i] = (float)g_uv[i];            // round to nearest
+        h_uv[i] = (float)src_uv[i];          // round to nearest
     for (size_t i = 0; i < h_w.size(); ++i)
         h_w[i] = (float)g_w[i];
-    if ((st = dev_alloc(&p->guv, h_uv.size())) != DG_OK ||
+    float **dst_uv = g_uv2 ? &p->guv2 : &p->guv;
+    if ((st = dev_alloc(dst_uv, h_uv.size())) != DG_OK ||
         (st = dev_alloc(&p->gw, h_w.size())) != DG_OK ||
         (st = dev_alloc(&p->status, 1)) != DG_OK ||
         (st = dev_alloc(&p->work_counter, 1)) != DG_OK ||
@@ -249,7 +258,7 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
         delete p;
         return st;
     }
-    cudaError_t e = cudaMemcpy(p->guv, h_uv.data(), sizeof(float) * h_uv.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(*dst_uv, h_uv.data(), sizeof(float) * h_uv.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p->gw, h_w.data(), sizeof(float) * h_w.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -265,6 +274,27 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     }
     *out = p;
     return DG_OK;
+}
+
+dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv,
+                             int uv_support, int uv_oversample, const double *g_w,
+                             int w_support, int w_oversample, dg_dtype dtype, int device)
+{
+    return plan_create(out, nx, ny, nz, g_uv, nullptr, uv_support, uv_oversample, g_w, w_support,
+                       w_oversample, dtype, device);
+}
+
+dg_status degrid_plan_create_2d(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv2,
+                                int uv_oversample, const double *g_w, int w_support, int w_oversample,
+                                dg_dtype dtype, int device)
+{
+    if (!g_uv2) {
+        if (out)
+            *out = nullptr;
+        return DG_ERR_ARG;
+    }
+    return plan_create(out, nx, ny, nz, nullptr, g_uv2, dg::kUV, uv_oversample, g_w, w_support,
+                       w_oversample, dtype, device);
 }
 
 void degrid_plan_destroy(degrid_plan_t p)
@@ -451,6 +481,8 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
 {
     if (!p || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
+    if (p->guv2)
+        return DG_ERR_UNSUPPORTED;          // gridding is built for the separable G_uv
     if (n_subgrids > 0 && !sub_out)
         return DG_ERR_ARG;
     if (n_vis > 0 && (!uvw || !vis_in || n_subgrids == 0))

@@ -133,6 +133,34 @@ __device__ __forceinline__ float2 quarter_sum(const float2 (&M)[2][8], const Row
     return __ffma2_rn(t1, make_float2(v.y, v.y), __fmul2_rn(t0, make_float2(v.x, v.x)));
 }
 
+// 2D G_uv table: this lane's quarter sum_{i} sum_a G[blk][2j + i][a] M[i][a]
+// with the 16 weights of rows 2j, 2j + 1 of the visibility's block read
+// straight from the (L2-resident) table.
+__device__ __forceinline__ float2 quarter_sum_2d(const float2 (&M)[2][8], const float *__restrict__ g2,
+                                                 int blk, int j)
+{
+    const float4 *w = reinterpret_cast<const float4 *>(g2 + (size_t)blk * (kUV * kUV) + 2 * kUV * j);
+    const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+    const float g0[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const float g1[8] = {w2.x, w2.y, w2.z, w2.w, w3.x, w3.y, w3.z, w3.w};
+    float2 t0 = __fmul2_rn(M[0][0], make_float2(g0[0], g0[0]));
+    float2 t1 = __fmul2_rn(M[1][0], make_float2(g1[0], g1[0]));
+#pragma unroll
+    for (int a = 1; a < 8; ++a) {
+        t0 = __ffma2_rn(M[0][a], make_float2(g0[a], g0[a]), t0);
+        t1 = __ffma2_rn(M[1][a], make_float2(g1[a], g1[a]), t1);
+    }
+    return __fadd2_rn(t0, t1);
+}
+
+// One pass: the separable sum from the staged rows, or the 2D table sum.
+template <bool T2D>
+__device__ __forceinline__ float2 pass_sum(const float2 (&M)[2][8], const RowStage &S,
+                                           const float *__restrict__ g2, int r, int blk, int j)
+{
+    return T2D ? quarter_sum_2d(M, g2, blk, j) : quarter_sum(M, S, r, j);
+}
+
 // Direct arm: this lane's quarter of visibility r (footprint `key`, w row gw)
 // from the subgrid itself, M's two rows formed on the fly; the same
 // operations in the same order as build_rows followed by quarter_sum.
@@ -181,12 +209,13 @@ struct MState {
 
 // Sums one half batch (32 visibilities, stage S, issued info I), reduces the
 // four lane partials and stores visibility `lane` of the half.
-template <int DT, bool COMP, bool DIRECT>
+template <int DT, bool COMP, bool DIRECT, bool T2D>
 __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStage &S, const Issued &I,
                                          const Batch &h, const void *__restrict__ subgrids, int64_t base,
                                          float sc, const Geometry &g, const float4 *wtab,
                                          const float *__restrict__ gwt, float2 *__restrict__ vis_out,
-                                         int direct_runs, bool vec_ok, int lane, int p, int j)
+                                         int direct_runs, bool vec_ok, const float *__restrict__ g2,
+                                         int lane, int p, int j)
 {
     float2 P[4];                        // pass k: this lane's quarter of visibility 8 (k ^ j) + p
     if (I.uniform) {
@@ -197,9 +226,11 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
             ms.fw = I.fw0;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            P[k] = quarter_sum(ms.M, S, 8 * (k ^ j) + p, j);
-    } else if (DIRECT && I.runs >= direct_runs) {
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * (k ^ j) + p;
+            P[k] = pass_sum<T2D>(ms.M, S, g2, r, T2D ? __shfl_sync(kFull, I.blk, r) : 0, j);
+        }
+    } else if (DIRECT && !T2D && I.runs >= direct_runs) {
         // Short runs: every visibility is summed from its own footprint
         // (pass k covers visibilities 8k .. 8k + 7; invalid ones stay zero).
         // Pays off when the footprints of a half overlap (slowly moving
@@ -253,7 +284,7 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
                     ms.key = lk;
                     ms.fw = lf;
                 }
-                const float2 x = quarter_sum(ms.M, S, r, j);
+                const float2 x = pass_sum<T2D>(ms.M, S, g2, r, T2D ? __shfl_sync(kFull, I.blk, r) : 0, j);
                 const bool mine = !done && kr == lk && fr == lf;
                 if (mine)
                     acc = x;
@@ -298,12 +329,13 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
         vis_out[h.b0 + lane] = V;
 }
 
-template <int DT, bool COMP, bool DIRECT>
+template <int DT, bool COMP, bool DIRECT, bool T2D>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_DEGRID_MIN_BLOCKS)
 degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *__restrict__ scale,
               const double *__restrict__ uvw, const float *__restrict__ guv,
               const float *__restrict__ gwt, const Schedule sched, float2 *__restrict__ vis_out,
-              DeviceStatus *__restrict__ status, const int direct_runs, const bool vec_ok)
+              DeviceStatus *__restrict__ status, const int direct_runs, const bool vec_ok,
+              const float *__restrict__ g2)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // [w table (optional)] [one WarpSmem per warp]
@@ -316,10 +348,10 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     Batch bB = claimer.claim();         // rows in flight
     if (bB.n == 0)
         return;
-    Issued iB0 = issue_rows(half_of(bB, 0), load_uvw(uvw, half_of(bB, 0), lane), g, ws.st[0][0], guv,
-                            lane, status, false);
-    Issued iB1 = issue_rows(half_of(bB, 1), load_uvw(uvw, half_of(bB, 1), lane), g, ws.st[0][1], guv,
-                            lane, status, true);
+    Issued iB0 = issue_rows<RowStage, !T2D>(half_of(bB, 0), load_uvw(uvw, half_of(bB, 0), lane), g,
+                                            ws.st[0][0], guv, lane, status, false);
+    Issued iB1 = issue_rows<RowStage, !T2D>(half_of(bB, 1), load_uvw(uvw, half_of(bB, 1), lane), g,
+                                            ws.st[0][1], guv, lane, status, true);
     Batch bC = claimer.advance(bB);     // coordinates in registers
     Coords3 cC0 = load_uvw(uvw, half_of(bC, 0), lane);
     Coords3 cC1 = load_uvw(uvw, half_of(bC, 1), lane);
@@ -343,8 +375,10 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
         const int sA = stage;
         bB = bC;
         if (bB.n > 0) {
-            iB0 = issue_rows(half_of(bB, 0), cC0, g, ws.st[sA ^ 1][0], guv, lane, status, false);
-            iB1 = issue_rows(half_of(bB, 1), cC1, g, ws.st[sA ^ 1][1], guv, lane, status, true);
+            iB0 = issue_rows<RowStage, !T2D>(half_of(bB, 0), cC0, g, ws.st[sA ^ 1][0], guv, lane, status,
+                                             false);
+            iB1 = issue_rows<RowStage, !T2D>(half_of(bB, 1), cC1, g, ws.st[sA ^ 1][1], guv, lane, status,
+                                             true);
         }
         bC = claimer.advance(bC);
         cC0 = load_uvw(uvw, half_of(bC, 0), lane);
@@ -362,11 +396,11 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
             if (DT != DG_C64)
                 sc = __ldg(scale + bA.s);
         }
-        sum_half<DT, COMP, DIRECT>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g, wtab, gwt,
-                           vis_out, direct_runs, vec_ok, lane, p, j);
+        sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g,
+                                        wtab, gwt, vis_out, direct_runs, vec_ok, g2, lane, p, j);
         if (bA.n > kBatch)
-            sum_half<DT, COMP, DIRECT>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc, g, wtab,
-                               gwt, vis_out, direct_runs, vec_ok, lane, p, j);
+            sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc,
+                                            g, wtab, gwt, vis_out, direct_runs, vec_ok, g2, lane, p, j);
         __syncwarp();
         stage ^= 1;
     }
@@ -377,13 +411,13 @@ size_t smem_bytes(const degrid_plan *p, int warps)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)warps;
 }
 
-template <int DT, bool COMP, bool DIRECT>
+template <int DT, bool COMP, bool DIRECT, bool T2D>
 cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                    const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT>,
+    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
@@ -391,44 +425,61 @@ cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const 
     // elements per 16 bytes
     const bool vec_ok = (reinterpret_cast<uintptr_t>(subgrids) & 15) == 0 &&
                         p->geo.nz % Storage<DT>::kQuad == 0;
-    degrid_kernel<DT, COMP, DIRECT><<<grid_blocks, threads, smem, st>>>(
-        p->geo, subgrids, scale, uvw, p->guv, p->gw, sched, out, p->status, p->direct_runs, vec_ok);
+    degrid_kernel<DT, COMP, DIRECT, T2D><<<grid_blocks, threads, smem, st>>>(
+        p->geo, subgrids, scale, uvw, p->guv, p->gw, sched, out, p->status, p->direct_runs, vec_ok,
+        p->guv2);
     return cudaGetLastError();
 }
 
-template <int DT, bool COMP, bool DIRECT>
+template <int DT, bool COMP, bool DIRECT, bool T2D>
 int max_blocks(degrid_plan *p)
 {
     int n = 0;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP, DIRECT>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP, DIRECT, T2D>,
                                                       p->warps_per_block * kWarp, smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+// Kernel instance of a plan: storage type, compensated reduction, and one of
+// three summing forms (footprint cache; with the direct arm; 2D G_uv table).
+template <int DT, bool COMP>
+cudaError_t launch_form(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
+                        const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
+{
+    if (p->guv2)
+        return launch<DT, COMP, false, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+    if (p->direct_runs < DG_DIRECT_RUNS_NEVER)
+        return launch<DT, COMP, true, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+    return launch<DT, COMP, false, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+}
+
+template <int DT, bool COMP>
+int max_blocks_form(degrid_plan *p)
+{
+    if (p->guv2)
+        return max_blocks<DT, COMP, false, true>(p);
+    if (p->direct_runs < DG_DIRECT_RUNS_NEVER)
+        return max_blocks<DT, COMP, true, false>(p);
+    return max_blocks<DT, COMP, false, false>(p);
 }
 
 template <int DT>
 cudaError_t launch_dt(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                       const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
-    const bool direct = p->direct_runs < DG_DIRECT_RUNS_NEVER;
-    if (p->compensated)
-        return direct ? launch<DT, true, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
-                      : launch<DT, true, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
-    return direct ? launch<DT, false, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
-                  : launch<DT, false, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
+    return p->compensated ? launch_form<DT, true>(p, st, subgrids, scale, uvw, out, sched, grid_blocks)
+                          : launch_form<DT, false>(p, st, subgrids, scale, uvw, out, sched, grid_blocks);
 }
 
 template <int DT>
 int max_blocks_dt(degrid_plan *p)
 {
-    const bool direct = p->direct_runs < DG_DIRECT_RUNS_NEVER;
-    if (p->compensated)
-        return direct ? max_blocks<DT, true, true>(p) : max_blocks<DT, true, false>(p);
-    return direct ? max_blocks<DT, false, true>(p) : max_blocks<DT, false, false>(p);
+    return p->compensated ? max_blocks_form<DT, true>(p) : max_blocks_form<DT, false>(p);
 }
 
 }  // namespace

@@ -199,6 +199,7 @@ struct degrid_plan {
     dg_dtype dtype;
     float *guv;                 // device FP32 [uv_os][8]
     float *gw;                  // device FP32 [w_os][4]
+    float *guv2;                // device FP32 [uv_os][uv_os][8][8] for a 2D G_uv table, else nullptr
     dg::DeviceStatus *status;   // device
     int *work_counter;          // device [1]
     int *n_chunks;              // device [1]

@@ -194,11 +194,14 @@ struct Issued {
     int key0, fw0;
     bool uniform;
     int runs;           // runs of equal (key, w row) among the valid visibilities (1 if uniform)
+    int blk;            // 2D G_uv table: weight block fv * O + fu of this visibility (0 if invalid)
 };
 
 // Stage 2 of a degridding batch: snap, and copy the g_u / g_v rows into the
 // stage (2 lanes per 32-byte row, so each row is one request).
-template <class Stage>
+// With kRows = false (a 2D G_uv table, read by the summing lanes themselves)
+// no rows are staged; the weight block index is kept instead.
+template <class Stage, bool kRows = true>
 __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, const Geometry &g,
                                              Stage &S, const float *__restrict__ guv, int lane,
                                              DeviceStatus *status, bool commit = true)
@@ -222,6 +225,12 @@ __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, c
     const unsigned bad = __ballot_sync(kFull, in && !valid);
     if (lane == 0 && bad)
         atomicAdd(&status->n_invalid, (unsigned long long)__popc(bad));
+    r.blk = (fv << g.log2_uv_os) + fu;
+    if (!kRows) {
+        if (commit)
+            cp_async_commit();
+        return r;
+    }
     const int half = lane & 1;
 #pragma unroll
     for (int m = 0; m < 2; ++m) {

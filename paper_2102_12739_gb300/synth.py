@@ -103,6 +103,29 @@ def gcf_table(support: int, oversample: int, beta: float) -> np.ndarray:
     return np.ascontiguousarray(kaiser_bessel(offs, support, beta))
 
 
+def gcf_table_2d(support: int, oversample: int, beta: float) -> np.ndarray:
+    """Oversampled non-separable G_uv: a circularly symmetric Kaiser-Bessel
+    kernel, float64 [oversample][oversample][support][support] indexed
+    [fv][fu][b][a], holding KB(sqrt(x^2 + y^2)) at x = (a - support/2 + 1) -
+    fu/oversample, y = (b - support/2 + 1) - fv/oversample (0 beyond radius
+    support/2)."""
+    f = np.arange(oversample, dtype=np.float64)
+    k = np.arange(support, dtype=np.float64)
+    off = (k[None, :] - support // 2 + 1) - f[:, None] / oversample        # [f][k]
+    y = off[:, None, :, None]                                             # [fv][1][b][1]
+    x = off[None, :, None, :]                                             # [1][fu][1][a]
+    r = np.sqrt(x * x + y * y)
+    return np.ascontiguousarray(kaiser_bessel(r, support, beta))
+
+
+TABLE2D_OVERSAMPLE = 64
+
+
+def default_table_2d(oversample: int = TABLE2D_OVERSAMPLE) -> np.ndarray:
+    """Circular Kaiser-Bessel G_uv table [O][O][8][8] (beta as the 1D table)."""
+    return gcf_table_2d(UV_SUPPORT, oversample, UV_BETA)
+
+
 def default_tables() -> tuple[np.ndarray, np.ndarray]:
     """(g_uv [16384][8], g_w [128][4]) Kaiser-Bessel tables, float64."""
     return (gcf_table(UV_SUPPORT, UV_OVERSAMPLE, UV_BETA),

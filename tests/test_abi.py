@@ -74,6 +74,13 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.degrid_plan_set_compensated(None, 1) == _native.DG_ERR_ARG
     assert lib.degrid_plan_get_compensated(None, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_direct_runs(None, 9) == _native.DG_ERR_ARG
+    # 2D G_uv plans: a table is required and its oversampling is bounded
+    t2 = np.zeros((4, 4, 8, 8))
+    c2 = t2.ctypes.data_as(P)
+    assert lib.degrid_plan_create_2d(ctypes.byref(h), 64, 64, 4, None, 4, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_create_2d(ctypes.byref(h), 64, 64, 4, c2, 512, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert lib.degrid_plan_create_2d(ctypes.byref(h), 64, 64, 4, c2, 6, b, 4, 128, 0, 0) == _native.DG_ERR_ARG
+    assert h.value is None
     assert lib.degrid_plan_get_direct_runs(None, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_tuning(None, 256, 8, 0) == _native.DG_ERR_ARG
     assert lib.degrid_get_status(None, None, None) == _native.DG_ERR_ARG
@@ -83,7 +90,7 @@ def test_host_argument_checks_need_no_gpu(lib):
 
 def test_header_constants_match_the_binding():
     text = open(HEADER).read()
-    for name in ("DG_DIRECT_RUNS_NEVER", "DG_DIRECT_RUNS_SHORT"):
+    for name in ("DG_DIRECT_RUNS_NEVER", "DG_DIRECT_RUNS_SHORT", "DG_TABLE2D_MAX_OVERSAMPLE"):
         m = re.search(r"#define\s+%s\s+(\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(_native, name)
     assert re.search(r"#define\s+DG_DIRECT_RUNS_DEFAULT\s+DG_DIRECT_RUNS_NEVER", text)
