@@ -557,6 +557,8 @@ def run_ours(args, rank, world):
         line["precision_sweep"] = sweep
 
     if not args.no_e2e:
+        # through the C-ABI call on HOST buffers (degrid_execute_host): the
+        # copies of each step's inputs and its output are inside the timing
         h_sub = torch.empty(sub.shape, dtype=sub.dtype, pin_memory=True)
         h_sub.copy_(torch.from_numpy(sub_np))
         h_uvw = torch.empty(uvw.shape, dtype=uvw.dtype, pin_memory=True)
@@ -567,19 +569,20 @@ def run_ours(args, rank, world):
         for i in range(args.e2e_steps + 2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            sub.copy_(h_sub, non_blocking=True)
-            uvw.copy_(h_uvw, non_blocking=True)
-            offs.copy_(h_offs, non_blocking=True)
-            plan.degrid(sub, uvw, offs, out=out)
-            h_out.copy_(out, non_blocking=True)
-            stream.synchronize()
+            plan.degrid_host(h_sub, h_uvw, h_offs, out=h_out)
             if i >= 2:
                 e2e_t.append(time.perf_counter() - t0)
+        assert plan.status() == 0
+        e2e_err = sampled_error(h_out.numpy(), w, g_uv, g_w, sub_np)
         bi = h_sub.numel() * h_sub.element_size() + h_uvw.numel() * 8 + h_offs.numel() * 8
         bo = h_out.numel() * h_out.element_size()
         line["e2e"] = {"value": w.n_vis / statistics.median(e2e_t), "unit": UNIT,
                        "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
-                       "path": "pinned host -> device copies, degrid_execute, device -> pinned host"}
+                       "rel_l2_vs_oracle": e2e_err[0],
+                       "path": "degrid_execute_host on pinned host buffers: subgrid groups of "
+                               "64 MB copied in, summed and copied out on three overlapping "
+                               "streams; the host-to-device link (about 209 GB/s on this box) "
+                               "bounds it"}
 
     if not args.no_adjoint:
         line["adjoint"] = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)

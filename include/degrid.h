@@ -226,6 +226,32 @@ dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
                          float *vis_out);
 
 /*
+ * degrid_execute with the inputs and the output in HOST memory (no
+ * counterpart in the paper, which starts from data on the GPU).  The call
+ * copies the subgrids, coordinates and offsets to the device, degrids and
+ * copies the visibilities back, overlapping the copies with the sums: the
+ * stack is processed in groups of consecutive subgrids (about 64 MB of
+ * subgrid data each) through two device slots, with the copy-in of one group,
+ * the sums of the previous one and the copy-out of the one before that on
+ * three streams of the plan.  Groups without visibilities are not copied.
+ * It returns when vis_out is complete (synchronous; the plan's streams are
+ * not the caller's).
+ *   subgrids, subgrid_scale, uvw, vis_offsets, vis_out   HOST pointers, the
+ *                  layouts of degrid_execute; page-locked (pinned) memory
+ *                  gives full copy bandwidth and overlap, pageable memory
+ *                  works at lower speed
+ * vis_offsets is checked on the host: DG_ERR_OFFSETS if vis_offsets[0] != 0,
+ * vis_offsets[S] != n_vis or it decreases.  The first call allocates the
+ * plan's streams and two staging slots (grown when a later call needs more);
+ * degrid_plan_destroy frees them.  Invalid visibilities are counted as for
+ * degrid_execute (read them with degrid_get_status).  Returns DG_OK,
+ * DG_ERR_ARG, DG_ERR_DTYPE, DG_ERR_OFFSETS, DG_ERR_OOM or DG_ERR_CUDA.
+ */
+dg_status degrid_execute_host(degrid_plan_t plan, int n_subgrids, const void *subgrids,
+                              const float *subgrid_scale, const double *uvw,
+                              const int64_t *vis_offsets, int64_t n_vis, float *vis_out);
+
+/*
  * Adjoint of degrid_execute (gridding): for every visibility i of subgrid s
  *   sub_out[s][y0+b][x0+a][z0+c] += g_uv[fv][b] g_uv[fu][a] g_w[fw][c] * vis_in[i]
  * (real weights, so the adjoint needs no conjugation).  sub_out is complex64

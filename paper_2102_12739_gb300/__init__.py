@@ -245,6 +245,51 @@ class DegridPlan:
         check(st, "degrid_execute")
         return out
 
+    def degrid_host(self, subgrids, uvw, vis_offsets, scale=None, out=None):
+        """degrid() on HOST data (degrid_execute_host): the call copies the
+        inputs to the device in subgrid groups, overlapping the copies with the
+        sums, and returns when the complex64 [N] host output is complete.
+
+        Inputs are CPU torch tensors or numpy arrays (subgrids complex64, or
+        for f16/bf16 plans the uint16 code pairs [S, ny, nx, nz, 2] with a
+        float32 scale [S]); pinned (page-locked) tensors give full bandwidth.
+        """
+        torch = _torch()
+
+        def cpu(x, dtype, name):
+            if not isinstance(x, torch.Tensor):
+                x = torch.from_numpy(np.ascontiguousarray(x))
+            if x.device.type != "cpu" or x.dtype != dtype or not x.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous CPU {dtype} tensor")
+            return x
+
+        sub_dtype = torch.complex64 if self.dtype == "c64" else (
+            torch.float16 if self.dtype == "f16" else torch.bfloat16)
+        if self.dtype != "c64" and isinstance(subgrids, np.ndarray):
+            subgrids = torch.from_numpy(np.ascontiguousarray(subgrids).view(np.int16)).view(sub_dtype)
+        sub = cpu(subgrids, sub_dtype, "subgrids")
+        S = sub.shape[0]
+        uvw = cpu(uvw, torch.float64, "uvw")
+        offs = cpu(vis_offsets, torch.int64, "vis_offsets")
+        n = uvw.shape[0]
+        if offs.shape != (S + 1,) or uvw.shape != (n, 3):
+            raise ValueError("vis_offsets must be [S + 1] and uvw [N, 3]")
+        sc = None
+        if self.dtype != "c64":
+            if scale is None:
+                raise ValueError("scale is required for f16/bf16 subgrids")
+            sc = cpu(scale, torch.float32, "scale")
+        if out is None:
+            out = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+        else:
+            out = cpu(out, torch.complex64, "out")
+            if out.shape != (n,):
+                raise ValueError("out must be [N]")
+        st = load().degrid_execute_host(self.handle, S, _vp(sub), _vp(sc), _vp(uvw), _vp(offs), n,
+                                        _vp(out))
+        check(st, "degrid_execute_host")
+        return out
+
     def grid(self, vis, uvw, vis_offsets, n_subgrids: int, out=None, accumulate: bool = False,
              stream=None):
         """Adjoint: complex64 [S, ny, nx, nz] from visibilities (grid_adjoint_execute)."""

@@ -43,6 +43,7 @@ SIGNATURES = {
     "degrid_plan_set_tuning": (_I, [_P, _I, _I, _I]),
     "degrid_plan_get_tuning": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "degrid_plan_create_2d": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P, _I, _P, _I, _I, _I, _I]),
+    "degrid_execute_host": (_I, [_P, _I, _P, _P, _P, _P, _I64, _P]),
     "degrid_plan_set_compensated": (_I, [_P, _I]),
     "degrid_plan_set_direct_runs": (_I, [_P, _I]),
     "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),

@@ -78,6 +78,7 @@ void free_events(degrid_plan *p)
 void free_plan_buffers(degrid_plan *p)
 {
     free_events(p);
+    dg_free_host_exec(p);
     cudaFree(p->guv);
     cudaFree(p->guv2);
     cudaFree(p->gw);

@@ -214,10 +214,13 @@ struct degrid_plan {
     int direct_runs;            // non-uniform halves with at least this many runs take the direct sum
     int max_blocks_degrid;      // occupancy results, 0 = not computed yet
     int max_blocks_adjoint;
+    struct dg_host_exec *hostx; // streams and staging of degrid_execute_host (host_exec.cu), lazily
     int n_slots;                // timing event pairs (0 = timing off)
     long long timed_launches;
     cudaEvent_t *ev_start, *ev_stop;
 };
+
+void dg_free_host_exec(degrid_plan *p);   // host_exec.cu
 
 // Kernel launchers (one per translation unit).
 cudaError_t dg_launch_degrid(degrid_plan *p, cudaStream_t st, const void *subgrids,

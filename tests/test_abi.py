@@ -74,6 +74,7 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.degrid_plan_set_compensated(None, 1) == _native.DG_ERR_ARG
     assert lib.degrid_plan_get_compensated(None, None) == _native.DG_ERR_ARG
     assert lib.degrid_plan_set_direct_runs(None, 9) == _native.DG_ERR_ARG
+    assert lib.degrid_execute_host(None, 1, None, None, None, None, 0, None) == _native.DG_ERR_ARG
     # 2D G_uv plans: a table is required and its oversampling is bounded
     t2 = np.zeros((4, 4, 8, 8))
     c2 = t2.ctypes.data_as(P)

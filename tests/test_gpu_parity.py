@@ -244,6 +244,38 @@ def test_direct_arm_is_bitwise_the_cached_path(kind):
     assert rel_l2(outs[1], ref) <= TOL["c64"]
 
 
+def test_host_memory_entry_point_matches_device_path():
+    # several subgrid groups (64 MB of subgrids each: 8 subgrids of 8 MB), an
+    # empty group in the middle, empty subgrids, invalid points; pinned and
+    # pageable host buffers; bitwise the device path's result
+    d = dev()
+    counts = [300, 0, 150, 1, 0, 77, 500, 20, 0, 0, 0, 0, 0, 0, 0, 0, 64, 9, 200]
+    w = small_workload(counts, kind="mixed", seed=61)
+    w.uvw[2] = [np.nan, 10.0, 1.5]
+    sub_np = synth.subgrid_stack(len(counts))
+    sub, uvw, offs = upload(w, sub_np)
+    with dg.DegridPlan(device=d) as p:
+        ref = p.degrid(sub, uvw, offs).cpu().numpy()
+        assert p.status() == 1
+        h_sub = torch.from_numpy(sub_np).pin_memory()
+        got = p.degrid_host(h_sub, torch.from_numpy(w.uvw).pin_memory(),
+                            torch.from_numpy(w.vis_offsets).pin_memory()).numpy()
+        assert p.status() == 1
+        np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+        again = p.degrid_host(sub_np, w.uvw, w.vis_offsets).numpy()     # pageable numpy
+        np.testing.assert_array_equal(again.view(np.uint32), ref.view(np.uint32))
+        assert p.status() == 1
+        bad = w.vis_offsets.copy()
+        bad[3] = bad[2] - 1                                              # decreasing
+        with pytest.raises(dg.DegridError):
+            p.degrid_host(sub_np, w.uvw, bad)
+    with dg.DegridPlan(dtype="f16", device=d) as p16:
+        codes, scale = dg.pack_subgrids(sub, "f16")
+        ref16 = p16.degrid(codes, uvw, offs, scale=scale).cpu().numpy()
+        got16 = p16.degrid_host(codes.cpu(), w.uvw, w.vis_offsets, scale=scale.cpu()).numpy()
+        np.testing.assert_array_equal(got16.view(np.uint32), ref16.view(np.uint32))
+
+
 @pytest.mark.parametrize("dtype", ["c64", "f16", "bf16"])
 def test_compensated_reduction(dtype):
     # the compensated form: same bar as the plain one, deterministic, and no
