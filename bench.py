@@ -47,8 +47,8 @@ FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 
 TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
                           "paper_2102_12739_gb300/csrc/pipeline.cuh",
                           "paper_2102_12739_gb300/csrc/internal.cuh")
-TRAFFIC_SHA = "c4d9f17b029b2c2e"
-TRAFFIC_BYTES_PER_VIS = (98.450944e6 + 11.691520e6) / 4_000_000
+TRAFFIC_SHA = "f1215e4a696ae2bc"
+TRAFFIC_BYTES_PER_VIS = (98.481408e6 + 11.677440e6) / 4_000_000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 
