@@ -209,6 +209,44 @@ struct MState {
 
 // Sums one half batch (32 visibilities, stage S, issued info I), reduces the
 // four lane partials and stores visibility `lane` of the half.
+// Reduces the four pass slots of every lane to visibility `lane` of the half
+// and stores it (times the subgrid's scale for FP16/BF16 storage).
+template <int DT, bool COMP>
+__device__ __forceinline__ void reduce_store(float2 (&P)[4], const Batch &h, float sc,
+                                             float2 *__restrict__ vis_out, int lane)
+{
+    // lane xor 16 (j ^ 2) brings slots 2, 3 onto 0, 1; lane xor 8 (j ^ 1)
+    // brings slot 1 onto 0
+    float2 V;
+    if (COMP) {
+        // the same three additions as error-free sums; the four rounding
+        // errors are summed and added back once
+        float2 e0, e1, e;
+        P[0].x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[2].x, 16), e0.x);
+        P[0].y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[2].y, 16), e0.y);
+        P[1].x = two_sum(P[1].x, __shfl_xor_sync(kFull, P[3].x, 16), e1.x);
+        P[1].y = two_sum(P[1].y, __shfl_xor_sync(kFull, P[3].y, 16), e1.y);
+        V.x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[1].x, 8), e.x);
+        V.y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[1].y, 8), e.y);
+        e.x += e0.x + __shfl_xor_sync(kFull, e1.x, 8);
+        e.y += e0.y + __shfl_xor_sync(kFull, e1.y, 8);
+        V.x += e.x;
+        V.y += e.y;
+    } else {
+        P[0].x += __shfl_xor_sync(kFull, P[2].x, 16);
+        P[0].y += __shfl_xor_sync(kFull, P[2].y, 16);
+        P[1].x += __shfl_xor_sync(kFull, P[3].x, 16);
+        P[1].y += __shfl_xor_sync(kFull, P[3].y, 16);
+        V.x = P[0].x + __shfl_xor_sync(kFull, P[1].x, 8);
+        V.y = P[0].y + __shfl_xor_sync(kFull, P[1].y, 8);
+    }
+    if (DT != DG_C64)
+        V = __fmul2_rn(V, make_float2(sc, sc));
+    if (lane < h.n)                     // lane 8j + p holds visibility 8j + p of the half
+        vis_out[h.b0 + lane] = V;
+}
+
+
 template <int DT, bool COMP, bool DIRECT, bool T2D>
 __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStage &S, const Issued &I,
                                          const Batch &h, const void *__restrict__ subgrids, int64_t base,
@@ -298,35 +336,36 @@ __device__ __forceinline__ void sum_half(MState &ms, WarpSmem &ws, const RowStag
             P[k] = ws.part[k ^ j][lane];
         __syncwarp();
     }
-    // lane xor 16 (j ^ 2) brings slots 2, 3 onto 0, 1; lane xor 8 (j ^ 1)
-    // brings slot 1 onto 0
-    float2 V;
-    if (COMP) {
-        // the same three additions as error-free sums; the four rounding
-        // errors are summed and added back once
-        float2 e0, e1, e;
-        P[0].x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[2].x, 16), e0.x);
-        P[0].y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[2].y, 16), e0.y);
-        P[1].x = two_sum(P[1].x, __shfl_xor_sync(kFull, P[3].x, 16), e1.x);
-        P[1].y = two_sum(P[1].y, __shfl_xor_sync(kFull, P[3].y, 16), e1.y);
-        V.x = two_sum(P[0].x, __shfl_xor_sync(kFull, P[1].x, 8), e.x);
-        V.y = two_sum(P[0].y, __shfl_xor_sync(kFull, P[1].y, 8), e.y);
-        e.x += e0.x + __shfl_xor_sync(kFull, e1.x, 8);
-        e.y += e0.y + __shfl_xor_sync(kFull, e1.y, 8);
-        V.x += e.x;
-        V.y += e.y;
-    } else {
-        P[0].x += __shfl_xor_sync(kFull, P[2].x, 16);
-        P[0].y += __shfl_xor_sync(kFull, P[2].y, 16);
-        P[1].x += __shfl_xor_sync(kFull, P[3].x, 16);
-        P[1].y += __shfl_xor_sync(kFull, P[3].y, 16);
-        V.x = P[0].x + __shfl_xor_sync(kFull, P[1].x, 8);
-        V.y = P[0].y + __shfl_xor_sync(kFull, P[1].y, 8);
+    reduce_store<DT, COMP>(P, h, sc, vis_out, lane);
+}
+
+// Both halves of a full step share one footprint and w row (the common
+// case on dense lists): their eight passes are summed in one block, so the
+// scheduler can interleave the two halves' loads and FMA chains.
+template <int DT, bool COMP, bool T2D>
+__device__ __forceinline__ void sum_step_uniform(MState &ms, WarpSmem &ws, const RowStage &S0,
+                                                 const RowStage &S1, const Issued &I0, const Issued &I1,
+                                                 const Batch &b, const void *__restrict__ subgrids,
+                                                 int64_t base, float sc, const Geometry &g,
+                                                 const float4 *wtab, const float *__restrict__ gwt,
+                                                 float2 *__restrict__ vis_out, bool vec_ok,
+                                                 const float *__restrict__ g2, int lane, int p, int j)
+{
+    if (I0.key0 != ms.key || I0.fw0 != ms.fw) {
+        const float4 gw = wtab ? wtab[I0.fw0] : __ldg(reinterpret_cast<const float4 *>(gwt) + I0.fw0);
+        build_rows<DT>(ms.M, ws.m, subgrids, base, I0.key0, gw, g, vec_ok, lane, j);
+        ms.key = I0.key0;
+        ms.fw = I0.fw0;
     }
-    if (DT != DG_C64)
-        V = __fmul2_rn(V, make_float2(sc, sc));
-    if (lane < h.n)                     // lane 8j + p holds visibility 8j + p of the half
-        vis_out[h.b0 + lane] = V;
+    float2 P0[4], P1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = 8 * (k ^ j) + p;
+        P0[k] = pass_sum<T2D>(ms.M, S0, g2, r, T2D ? __shfl_sync(kFull, I0.blk, r) : 0, j);
+        P1[k] = pass_sum<T2D>(ms.M, S1, g2, r, T2D ? __shfl_sync(kFull, I1.blk, r) : 0, j);
+    }
+    reduce_store<DT, COMP>(P0, half_of(b, 0), sc, vis_out, lane);
+    reduce_store<DT, COMP>(P1, half_of(b, 1), sc, vis_out, lane);
 }
 
 template <int DT, bool COMP, bool DIRECT, bool T2D>
@@ -396,11 +435,18 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
             if (DT != DG_C64)
                 sc = __ldg(scale + bA.s);
         }
-        sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc, g,
-                                        wtab, gwt, vis_out, direct_runs, vec_ok, g2, lane, p, j);
-        if (bA.n > kBatch)
-            sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base, sc,
+        if (iA0.uniform && iA1.uniform && iA0.key0 == iA1.key0 && iA0.fw0 == iA1.fw0 &&
+            bA.n == kBatchVis) {
+            sum_step_uniform<DT, COMP, T2D>(ms, ws, ws.st[sA][0], ws.st[sA][1], iA0, iA1, bA, subgrids,
+                                            base, sc, g, wtab, gwt, vis_out, vec_ok, g2, lane, p, j);
+        } else {
+            sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][0], iA0, half_of(bA, 0), subgrids, base, sc,
                                             g, wtab, gwt, vis_out, direct_runs, vec_ok, g2, lane, p, j);
+            if (bA.n > kBatch)
+                sum_half<DT, COMP, DIRECT, T2D>(ms, ws, ws.st[sA][1], iA1, half_of(bA, 1), subgrids, base,
+                                                sc, g, wtab, gwt, vis_out, direct_runs, vec_ok, g2, lane,
+                                                p, j);
+        }
         __syncwarp();
         stage ^= 1;
     }
