@@ -238,6 +238,18 @@ def warm_up(torch, call, flush_buf, steps, min_seconds=1.0):
     torch.cuda.synchronize()
 
 
+def warm_kernel_ms(torch, plan, call, steps):
+    """Median main-kernel time with warm caches (no flush between calls)."""
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    plan.kernel_times_ms(1)
+    for _ in range(steps):
+        call()
+    ms = sorted(plan.kernel_times_ms(steps))
+    return ms[len(ms) // 2]
+
+
 def time_steps(torch, plan, call, steps, flush_buf, stream):
     """Run `steps` calls with an L2 flush before each; return per-step event
     times (ms) and per-launch main-kernel times (ms)."""
@@ -499,12 +511,24 @@ def run_ours(args, rank, world):
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = w.n_vis * FLOP_PER_VIS / (mean_kern * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+    # the other bound of the direct method: compulsory DRAM bytes (coordinates,
+    # output, every touched subgrid element once) against the measured copy rate
+    import oracle
+    touched = int(oracle.touched(w.shape, w.n_subgrids, w.uvw, w.vis_offsets).sum())
+    hbm_bytes = w.n_vis * (24 + 8) + touched * 8
+    hbm_ms = hbm_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    alu_ms = w.n_vis * FLOP_PER_VIS / (peak_tflops * 1e12) * 1e3
+    roofline = {"bound": "alu" if alu_ms >= hbm_ms else "hbm", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": measured_traffic(w.n_vis),
                 "kernel": "degrid_kernel<DG_C64>",
                 "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
                                f"lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
-                "kernel_ms": mean_kern}
+                "kernel_ms": mean_kern,
+                "bounds_ms": {"alu": alu_ms, "hbm": hbm_ms,
+                              "hbm_bytes": hbm_bytes, "hbm_gbs": peaks["hbm_gbs"],
+                              "touched_subgrid_elements": touched},
+                "warm_kernel_ms": warm_kernel_ms(torch, plan, step, 200)}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
