@@ -61,6 +61,8 @@ def _load():
             lib.oracle_grid.restype = _I64
             lib.oracle_grid.argtypes = ([_I32] * 3 + [_P, _I32, _I32, _P, _I32, _I32,
                                                       _I32, _P, _P, _I64, _P, _P, _I32])
+            lib.oracle_grid_2d.restype = _I64
+            lib.oracle_grid_2d.argtypes = lib.oracle_grid.argtypes
             lib.oracle_touched.restype = _I64
             lib.oracle_touched.argtypes = [_I32] * 8 + [_P, _P, _I64, _P]
             lib.oracle_set_threads.restype = None
@@ -178,6 +180,30 @@ def grid(g_uv, g_w, shape, n_subgrids, uvw, vis_offsets, vis, out=None):
                               int(accumulate))
     if bad < 0:
         raise ValueError("oracle_grid: invalid vis_offsets")
+    return out, int(bad)
+
+
+def grid_2d(g_uv2, g_w, shape, n_subgrids, uvw, vis_offsets, vis, out=None):
+    """Adjoint of ``degrid_2d``: complex128 [S][ny][nx][nz] and the invalid
+    count (added to ``out`` if given)."""
+    g_uv2 = np.ascontiguousarray(g_uv2, dtype=np.float64)
+    O, O2, W, W2 = g_uv2.shape
+    assert O == O2 and W == W2
+    g_w = np.ascontiguousarray(g_w, dtype=np.float64)
+    ny, nx, nz = shape
+    uvw = _f64(uvw).reshape(-1, 3)
+    offs = np.ascontiguousarray(vis_offsets, dtype=np.int64)
+    y = _complex_to_pairs(vis).reshape(-1, 2)
+    accumulate = out is not None
+    if out is None:
+        out = np.empty((n_subgrids, ny, nx, nz), dtype=np.complex128)
+    assert out.dtype == np.complex128 and out.flags.c_contiguous
+    buf = out.view(np.float64)
+    bad = _load().oracle_grid_2d(nx, ny, nz, _ptr(g_uv2), W, O, _ptr(g_w), g_w.shape[1],
+                                 g_w.shape[0], n_subgrids, _ptr(uvw), _ptr(offs), uvw.shape[0],
+                                 _ptr(y), _ptr(buf), int(accumulate))
+    if bad < 0:
+        raise ValueError("oracle_grid_2d: invalid vis_offsets")
     return out, int(bad)
 
 

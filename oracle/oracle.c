@@ -266,6 +266,49 @@ int64_t oracle_grid(int nx, int ny, int nz,
     return bad;
 }
 
+/* Adjoint of oracle_degrid_2d (gridding with a non-separable G_uv):
+ * grid_out[s][y0+b][x0+a][z0+c] += G[fv][fu][b][a] g_w[fw][c] vis_in[i], with
+ * g_uv2 [O][O][W][W] indexed [fv][fu][b][a] as in oracle_degrid_2d. */
+int64_t oracle_grid_2d(int nx, int ny, int nz,
+                       const double *g_uv2, int uv_support, int uv_oversample,
+                       const double *g_w, int w_support, int w_oversample,
+                       int n_subgrids, const double *uvw, const int64_t *vis_offsets,
+                       int64_t n_vis, const double *vis_in, double *grid_out,
+                       int accumulate)
+{
+    if (!offsets_ok(n_subgrids, vis_offsets, n_vis))
+        return -1;
+    const int64_t plane = (int64_t)ny * nx * nz;
+    const int64_t block = (int64_t)uv_support * uv_support;
+    if (!accumulate)
+        memset(grid_out, 0, sizeof(double) * 2 * plane * n_subgrids);
+    int64_t bad = 0;
+#pragma omp parallel for reduction(+ : bad) schedule(dynamic, 1)
+    for (int s = 0; s < n_subgrids; ++s) {
+        double *sg = grid_out + 2 * plane * s;
+        for (int64_t i = vis_offsets[s]; i < vis_offsets[s + 1]; ++i) {
+            coords_t c;
+            if (!visibility_coords(uvw + 3 * i, nx, ny, nz, uv_support, uv_oversample,
+                                   w_support, w_oversample, &c)) {
+                bad += 1;
+                continue;
+            }
+            const double *G = g_uv2 + ((int64_t)c.fv * uv_oversample + c.fu) * block;
+            const double *gw = g_w + c.fw * w_support;
+            const double yre = vis_in[2 * i], yim = vis_in[2 * i + 1];
+            for (int b = 0; b < uv_support; ++b)
+                for (int a = 0; a < uv_support; ++a)
+                    for (int k = 0; k < w_support; ++k) {
+                        double w = G[b * uv_support + a] * gw[k];
+                        int64_t e = ((c.y0 + b) * nx + (c.x0 + a)) * nz + (c.z0 + k);
+                        sg[2 * e] += w * yre;
+                        sg[2 * e + 1] += w * yim;
+                    }
+        }
+    }
+    return bad;
+}
+
 /* Number of distinct subgrid elements touched by the footprints of each
  * subgrid's valid visibilities (the compulsory subgrid bytes of a
  * degridding pass are this count times the element size). */

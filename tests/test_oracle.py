@@ -398,3 +398,41 @@ def test_2d_constant_subgrid_is_block_sum():
     expect = c * G[fv, fu].sum(axis=(1, 2)) * G_W[fw].sum(1)
     expect[7] = 0
     np.testing.assert_allclose(vis, expect, rtol=1e-12, atol=1e-12)
+
+
+def test_2d_adjoint_dot_product_identity():
+    # <D s, y> = <s, G y> for the 2D table with a random (non-separable) G
+    shape = (28, 36, 4)
+    rng = np.random.default_rng(45)
+    G = rng.standard_normal((O2D, O2D, 8, 8))
+    sub = random_subgrids(rng, 2, shape)
+    parts = [synth.piecewise_list(150, np.random.default_rng([45, s]), shape) for s in range(2)]
+    uvw = np.concatenate(parts)
+    uvw[5] = [np.nan, 4.0, 1.5]
+    offs = [0, 150, 300]
+    y = rng.standard_normal(300) + 1j * rng.standard_normal(300)
+    ds, bad1 = oracle.degrid_2d(G, G_W, sub, uvw, offs)
+    gy, bad2 = oracle.grid_2d(G, G_W, shape, 2, uvw, offs, y)
+    assert bad1 == bad2 == 1
+    lhs = np.vdot(ds, y)
+    rhs = np.vdot(sub, gy)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_2d_adjoint_one_hot_block_scatters_one_sample():
+    # one visibility, one-hot block (b*, a*) and one-hot w row: exactly one
+    # subgrid element receives y, at the footprint start + (b*, a*, k*)
+    shape = (24, 24, 4)
+    bstar, astar = _onehot_positions(O2D)
+    G = np.zeros((O2D, O2D, 8, 8))
+    fv_i, fu_i = np.meshgrid(np.arange(O2D), np.arange(O2D), indexing="ij")
+    G[fv_i, fu_i, bstar, astar] = 1.0
+    g_w = np.zeros_like(G_W)
+    g_w[5, 3] = 1.0
+    fu, fv = 17, 42
+    uvw = np.array([[9 + fu / O2D, 11 + fv / O2D, 1.0 + 5 / 128.0]])
+    out, bad = oracle.grid_2d(G, g_w, shape, 1, uvw, [0, 1], np.array([2.5 - 1.5j]))
+    assert bad == 0
+    nz = np.argwhere(out != 0)
+    assert nz.tolist() == [[0, 11 - 3 + bstar[fv, fu], 9 - 3 + astar[fv, fu], 3]]
+    assert out[0, 11 - 3 + bstar[fv, fu], 9 - 3 + astar[fv, fu], 3] == 2.5 - 1.5j

@@ -29,6 +29,8 @@ MUTANTS = {
     "bounds_off_by_one": ("return s >= 0 && s <= (long long)n - W;", "return s >= 0 && s <= (long long)n - W + 1;"),
     "2d_offsets_swapped": ("((int64_t)c.fv * uv_oversample + c.fu) * block;", "((int64_t)c.fu * uv_oversample + c.fv) * block;"),
     "2d_block_transposed": ("double w = G[b * uv_support + a] * gw[k];", "double w = G[a * uv_support + b] * gw[k];"),
+    "2d_adjoint_block_transposed": ("double w = G[b * uv_support + a] * gw[k];\n                        int64_t e = ((c.y0 + b) * nx + (c.x0 + a)) * nz + (c.z0 + k);\n                        sg[2 * e] += w * yre;",
+                                    "double w = G[a * uv_support + b] * gw[k];\n                        int64_t e = ((c.y0 + b) * nx + (c.x0 + a)) * nz + (c.z0 + k);\n                        sg[2 * e] += w * yre;"),
     "2d_x_y_transposed": ("double w = G[b * uv_support + a] * gw[k];\n                            int64_t e = ((c.y0 + b) * nx + (c.x0 + a)) * nz + (c.z0 + k);",
                           "double w = G[b * uv_support + a] * gw[k];\n                            int64_t e = ((c.x0 + a) * nx + (c.y0 + b)) * nz + (c.z0 + k);"),
 }
