@@ -112,9 +112,8 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz,
  *   uv_oversample  power of two, 1 .. DG_TABLE2D_MAX_OVERSAMPLE (the FP32
  *                  table, uv_oversample^2 * 256 bytes, stays L2-resident)
  * and the other arguments as for degrid_plan_create (support 8 implied).
- * degrid_execute (all storage types, compensated or not) uses the 2D table;
- * grid_adjoint_execute returns DG_ERR_UNSUPPORTED for such a plan and the
- * direct summing arm is not used.
+ * degrid_execute (all storage types, compensated or not) and
+ * grid_adjoint_execute use the 2D table; the direct summing arm is not used.
  */
 #define DG_TABLE2D_MAX_OVERSAMPLE 256
 dg_status degrid_plan_create_2d(degrid_plan_t *out, int nx, int ny, int nz, const double *g_uv2,
@@ -257,8 +256,8 @@ dg_status degrid_execute_host(degrid_plan_t plan, int n_subgrids, const void *su
  * (real weights, so the adjoint needs no conjugation).  sub_out is complex64
  * [S][ny][nx][nz] on the DEVICE, zeroed first unless accumulate != 0.
  * FP32 atomic accumulation: the summation order, and so the last bits, are
- * not deterministic.  Other arguments as for degrid_execute.  A plan made by
- * degrid_plan_create_2d gives DG_ERR_UNSUPPORTED.
+ * not deterministic.  Other arguments as for degrid_execute.  With a plan made
+ * by degrid_plan_create_2d the weights are G[fv][fu][b][a] g_w[fw][c].
  */
 dg_status grid_adjoint_execute(degrid_plan_t plan, void *stream, int n_subgrids,
                                const double *uvw, const int64_t *vis_offsets,

@@ -1,6 +1,7 @@
 // Adjoint of degridding (gridding): scatter every visibility back onto its
 // 8 x 8 x 4 footprint with the weights of the forward sum,
-//   sub[s][y0+b][x0+a][z0+c] += g_v[b] g_u[a] g_w[c] * vis[i].
+//   sub[s][y0+b][x0+a][z0+c] += g_v[b] g_u[a] g_w[c] * vis[i]
+// (or G[fv][fu][b][a] g_w[c] * vis[i] with a non-separable 2D G_uv table).
 // The weights are real, so this is the exact transpose of degrid.cu.
 //
 // The batch pipeline is the forward kernel's (pipeline.cuh): lane i of a
@@ -57,6 +58,34 @@ __device__ __forceinline__ void accumulate(float2 (&T)[2][8], const RowStage &S,
     }
 }
 
+// 2D G_uv table: T[i][a] += G[blk][2j + i][a] * y for the visibility whose
+// weight block is blk (16 weights of rows 2j, 2j + 1 read from the table).
+__device__ __forceinline__ void accumulate_2d(float2 (&T)[2][8], const float *__restrict__ g2, int blk,
+                                              int j, float2 y)
+{
+    const float4 *w = reinterpret_cast<const float4 *>(g2 + (size_t)blk * (kUV * kUV) + 2 * kUV * j);
+    const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+    const float g0[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const float g1[8] = {w2.x, w2.y, w2.z, w2.w, w3.x, w3.y, w3.z, w3.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        T[0][a] = __ffma2_rn(make_float2(g0[a], g0[a]), y, T[0][a]);
+        T[1][a] = __ffma2_rn(make_float2(g1[a], g1[a]), y, T[1][a]);
+    }
+}
+
+// One visibility of a pass: the separable rows from the stage, or the 2D table.
+template <bool T2D>
+__device__ __forceinline__ void accumulate_vis(float2 (&T)[2][8], const RowStage &S,
+                                               const float *__restrict__ g2, int r, int blk, int j,
+                                               float2 y)
+{
+    if (T2D)
+        accumulate_2d(T, g2, blk, j, y);
+    else
+        accumulate(T, S, r, j, y);
+}
+
 // Adds the run (key, fw) to the subgrid at sub_s and clears T.
 __device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *__restrict__ sub_s,
                                       int key, int fw, const Geometry &g, const float4 *wtab,
@@ -91,10 +120,12 @@ __device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *_
     atomicAdd(e1 + 3, make_float2(sum.z * gw.w, sum.w * gw.w));
 }
 
+template <bool T2D>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_ADJOINT_MIN_BLOCKS)
 adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *__restrict__ vis_in,
                const float *__restrict__ guv, const float *__restrict__ gwt, const Schedule sched,
-               float2 *__restrict__ sub_out, DeviceStatus *__restrict__ status)
+               float2 *__restrict__ sub_out, DeviceStatus *__restrict__ status,
+               const float *__restrict__ g2)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     WarpSmem &ws = reinterpret_cast<WarpSmem *>(smem_raw + wtable_bytes(g))[threadIdx.x >> 5];
@@ -106,7 +137,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
     Batch bB = claimer.claim();
     if (bB.n == 0)
         return;
-    Issued iB = issue_rows(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
+    Issued iB = issue_rows<RowStage, !T2D>(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
     float2 yB = load_y(vis_in, bB, lane);
     Batch bC = claimer.advance(bB);
     Coords3 cC = load_uvw(uvw, bC, lane);
@@ -126,7 +157,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
         const int sA = stage;
         bB = bC;
         if (bB.n > 0) {
-            iB = issue_rows(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
+            iB = issue_rows<RowStage, !T2D>(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
             yB = load_y(vis_in, bB, lane);
         }
         bC = claimer.advance(bC);
@@ -158,7 +189,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
                 float2 y;
                 y.x = __shfl_sync(kFull, yA.x, r);
                 y.y = __shfl_sync(kFull, yA.y, r);
-                accumulate(T, S, r, j, y);
+                accumulate_vis<T2D>(T, S, g2, r, T2D ? __shfl_sync(kFull, iA.blk, r) : 0, j, y);
             }
         } else {
             // visibilities in list order; each change of (footprint, w row)
@@ -168,6 +199,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
                 const int r = 8 * k + p;
                 const int kr = __shfl_sync(kFull, iA.key, r);
                 const int fr = __shfl_sync(kFull, iA.fw, r);
+                const int br = T2D ? __shfl_sync(kFull, iA.blk, r) : 0;
                 float2 y;
                 y.x = __shfl_sync(kFull, yA.x, r);
                 y.y = __shfl_sync(kFull, yA.y, r);
@@ -187,7 +219,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
                         run_fw = lf;
                     }
                     const bool mine = !done && kr == lk && fr == lf;
-                    accumulate(T, S, r, j, mine ? y : make_float2(0.f, 0.f));
+                    accumulate_vis<T2D>(T, S, g2, r, br, j, mine ? y : make_float2(0.f, 0.f));
                     done = done || mine;
                 }
             }
@@ -215,13 +247,13 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
     (void)vis_offsets;
     Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const size_t smem = smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    adjoint_kernel<<<grid_blocks, p->warps_per_block * kWarp, smem, st>>>(
+    kernel<<<grid_blocks, p->warps_per_block * kWarp, smem, st>>>(
         p->geo, uvw, reinterpret_cast<const float2 *>(vis_in), p->guv, p->gw, sched,
-        reinterpret_cast<float2 *>(sub_out), p->status);
+        reinterpret_cast<float2 *>(sub_out), p->status, p->guv2);
     return cudaGetLastError();
 }
 
@@ -230,11 +262,11 @@ int dg_max_blocks_per_sm_adjoint(degrid_plan *p)
     using namespace dg;
     int n = 0;
     const size_t smem = smem_bytes(p);
-    if (cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel, p->warps_per_block * kWarp,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, p->warps_per_block * kWarp, smem) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }

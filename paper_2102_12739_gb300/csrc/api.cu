@@ -482,8 +482,6 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
 {
     if (!p || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
-    if (p->guv2)
-        return DG_ERR_UNSUPPORTED;          // gridding is built for the separable G_uv
     if (n_subgrids > 0 && !sub_out)
         return DG_ERR_ARG;
     if (n_vis > 0 && (!uvw || !vis_in || n_subgrids == 0))

@@ -341,11 +341,35 @@ def test_table2d_matches_oracle(kind, dtype):
         # the coordinate step uses the 2D table's oversampling
         c, _ = oracle.coords(w.uvw, SHAPE, 8, G2.shape[0], 4, 128)
         np.testing.assert_array_equal(p.coords(uvw).cpu().numpy(), c)
-        with pytest.raises(dg.DegridError):      # gridding is built for separable tables
-            p.grid(torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(d), uvw, offs, w.n_subgrids)
     ref, bad = oracle.degrid_2d(G2, G_W, ref_sub, w.uvw, w.vis_offsets)
     assert bad == 1 and got[4] == 0
     assert rel_l2(got, ref) <= 2e-6       # kernel error (the oracle reads the stored values)
+
+
+@pytest.mark.parametrize("kind", ["line", "scatter", "mixed"])
+def test_table2d_adjoint_matches_oracle(kind):
+    d = dev()
+    shape = (40, 72, 4)
+    rng = np.random.default_rng(53)
+    G2 = rng.standard_normal((32, 32, 8, 8))          # a non-separable table
+    w = small_workload([640, 0, 257, 33], kind=kind, shape=shape, seed=53)
+    w.uvw[6] = [np.nan, 10.0, 1.5]
+    y = synth.adjoint_vis(w.n_vis)
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    sub_np = synth.subgrid_stack(4, shape)
+    with dg.DegridPlan(shape=shape, device=d, g_uv2=G2) as p:
+        got = p.grid(torch.from_numpy(y).to(d), uvw, offs, w.n_subgrids).cpu().numpy()
+        assert p.status() == 1
+        ds = p.degrid(torch.from_numpy(sub_np).to(d), uvw, offs).cpu().numpy()
+        assert p.status() == 1
+    ref, bad = oracle.grid_2d(G2, G_W, shape, w.n_subgrids, w.uvw, w.vis_offsets, y)
+    assert bad == 1
+    assert rel_l2(got, ref) <= TOL["c64"]
+    # the GPU pair is an adjoint pair: <D s, y> = <s, G y>
+    lhs = np.vdot(ds.astype(np.complex128), y.astype(np.complex128))
+    rhs = np.vdot(sub_np.astype(np.complex128), got.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
 def test_table2d_separable_equals_separable_path():
