@@ -2,13 +2,14 @@
 //
 // A persistent grid of warps claims chunks of consecutive visibilities of
 // one subgrid (schedule.cu; claims pipelined one chunk ahead) and walks each
-// chunk in batches of 32.  For every batch, lane i snaps visibility i (exact
-// integer rint of its FP64 coordinates, internal.cuh), keeps its footprint
-// key and w-kernel row in registers, and copies its g_u and g_v rows into
-// the warp's shared-memory stage with cp.async; the small w table is kept in
-// the CTA's shared memory.  The paper's D1 likewise computes the coordinates of all
-// N_b visibilities of a block cooperatively into shared memory before the
-// sums (Section "Implementation").
+// chunk in batches of 32 visibilities (the gridding kernel) or steps of two
+// such halves (the degridding kernel).  For every batch, lane i snaps
+// visibility i (exact integer rint of its FP64 coordinates, internal.cuh),
+// keeps its footprint key and w-kernel row in registers, and copies its g_u
+// and g_v rows into the warp's shared-memory stage with cp.async; the small w
+// table is kept in the CTA's shared memory.  The paper's D1 likewise computes
+// the coordinates of all N_b visibilities of a block cooperatively into
+// shared memory before the sums (Section "Implementation").
 #pragma once
 
 #include "internal.cuh"
@@ -42,7 +43,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 struct Batch {
     int s;          // subgrid
-    int n;          // visibilities in this batch (1..32), 0 = none
+    int n;          // visibilities in this batch (1..kStep), 0 = none
     long long b0;   // first visibility
     long long end;  // end of the chunk
 };
