@@ -26,7 +26,7 @@ namespace dg {
 namespace {
 
 #ifndef DG_ADJOINT_MIN_BLOCKS
-#define DG_ADJOINT_MIN_BLOCKS 3
+#define DG_ADJOINT_MIN_BLOCKS 2   // resident CTAs per SM the register budget (128) is sized for
 #endif
 
 constexpr int kMaxWarps = 8;
