@@ -47,8 +47,8 @@ FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 
 TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
                           "paper_2102_12739_gb300/csrc/pipeline.cuh",
                           "paper_2102_12739_gb300/csrc/internal.cuh")
-TRAFFIC_SHA = "8daef2b66da3e2d9"
-TRAFFIC_BYTES_PER_VIS = (98.479872e6 + 11.611392e6) / 4_000_000
+TRAFFIC_SHA = "350e09c75a841ec2"
+TRAFFIC_BYTES_PER_VIS = (98.479104e6 + 11.637760e6) / 4_000_000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 # (chunk, warps per CTA, CTAs per SM, direct-arm threshold) tried on the headline workload
@@ -185,6 +185,7 @@ def run_reference(args, rank, world):
         "config": {"workload": WORKLOAD + ": " + WORKLOAD_DESC,
                    "step": "FP64 CPU oracle over subgrid 0 (250,000 visibilities)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu": cpu_model(), "nproc": os.cpu_count(),
                          "sample": "subgrid 0 of the workload, 250,000 visibilities per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -195,6 +196,26 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------
 
+def cpu_model() -> str:
+    """Host CPU model (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(w, g_uv, g_w):
     """The FP64 oracle, as it stands, over the whole workload once."""
     import oracle
@@ -203,6 +224,7 @@ def cpu_baseline(w, g_uv, g_w):
     _, bad = oracle.degrid(g_uv, g_w, sub, w.uvw, w.vis_offsets)
     dt = time.perf_counter() - t0
     return {"value": w.n_vis / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "cpu": cpu_model(), "nproc": os.cpu_count(),
             "sample": f"the whole workload once ({w.n_vis} visibilities, {dt:.2f} s)"}
 
 
@@ -346,6 +368,34 @@ def scatter_section(torch, dg, synth, dev, flush, steps):
     return {"workload": "scatter16_250k: 16 subgrids 512x512x4, 250,000 visibilities each "
                         "scattered uniformly over the valid box (no footprint shared by "
                         "consecutive visibilities)", "unit": UNIT, "steps": steps, "by_storage": res}
+
+
+def latency_section(torch, dg, synth, dev, steps):
+    """The smallest configuration (1 subgrid, 20,000 visibilities on a line):
+    time of one degrid_execute call, schedule included, inputs in HBM."""
+    w = synth.workload("line1_20k")
+    sub = torch.from_numpy(synth.subgrid_stack(1)).to(dev)
+    uvw = torch.from_numpy(w.uvw).to(dev)
+    offs = torch.from_numpy(w.vis_offsets).to(dev)
+    out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with dg.DegridPlan(device=dev) as plan:
+        for _ in range(20):
+            plan.degrid(sub, uvw, offs, out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            a.record(stream)
+            plan.degrid(sub, uvw, offs, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    return {"workload": "line1_20k: 1 subgrid 512x512x4, 20,000 visibilities on one line",
+            "call_us": ms[len(ms) // 2] * 1e3, "value": w.n_vis / (ms[len(ms) // 2] * 1e-3),
+            "unit": UNIT, "steps": steps,
+            "call_includes": "offset validation and chunk scan, chunk table, degridding kernel"}
 
 
 def table2d_section(torch, dg, synth, dev, flush, steps, sub, sub_np, uvw, offs, w):
@@ -515,7 +565,11 @@ def run_ours(args, rank, world):
 
     props = torch.cuda.get_device_properties(dev)
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    analytic_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # the FP32 peak measured on this GPU (FFMA2 and FFMA chain kernels), the higher of the two
+    measured_fp32 = {"ffma2": dg.measure_fp32_peak(local, packed=True),
+                     "ffma": dg.measure_fp32_peak(local, packed=False)}
+    peak_tflops = max(measured_fp32.values())
     achieved = w.n_vis * FLOP_PER_VIS / (mean_kern * 1e-3) / 1e12
     # the other bound of the direct method: compulsory DRAM bytes (coordinates,
     # output, every touched subgrid element once) against the measured copy rate
@@ -528,8 +582,12 @@ def run_ours(args, rank, world):
                 "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": measured_traffic(w.n_vis),
                 "kernel": "degrid_kernel<DG_C64>",
-                "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 "
-                               f"lanes x 2 flop x {sm_max:.0f} MHz (unit counts and max clock)",
+                "peak_source": "measured: the faster of FFMA2 and FFMA chain kernels filling "
+                               "every SM (degrid_measure_fp32_peak), TFLOP/s %s" % (
+                                   {k: round(v, 2) for k, v in measured_fp32.items()},),
+                "peak_analytic": analytic_tflops,
+                "peak_analytic_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} "
+                                        f"FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                 "kernel_ms": mean_kern,
                 "bounds_ms": {"alu": alu_ms, "hbm": hbm_ms,
                               "hbm_bytes": hbm_bytes, "hbm_gbs": peaks["hbm_gbs"],
@@ -623,6 +681,8 @@ def run_ours(args, rank, world):
 
     if not args.no_adjoint:
         line["adjoint"] = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)
+
+    line["latency"] = latency_section(torch, dg, synth, dev, args.aux_steps)
 
     if not args.no_table2d:
         line["table2d"] = table2d_section(torch, dg, synth, dev, flush, args.aux_steps, sub, sub_np,

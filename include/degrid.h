@@ -182,7 +182,7 @@ dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_
  * Kernel timing (profiling aid, not in the paper).  degrid_plan_enable_timing
  * with n_slots > 0 creates n_slots CUDA event pairs; from then on every
  * degrid_execute / grid_adjoint_execute records one pair on its stream around
- * its main (persistent) kernel only, excluding the two small scheduling
+ * its main (persistent) kernel only, excluding the small scheduling
  * kernels, cycling through the slots.  n_slots = 0 disables timing and frees
  * the events.  Disable timing before capturing calls into a CUDA graph.
  *
@@ -195,6 +195,20 @@ dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_
 dg_status degrid_plan_enable_timing(degrid_plan_t plan, int n_slots);
 dg_status degrid_plan_kernel_times_ms(degrid_plan_t plan, float *ms_out, int capacity,
                                       int *count);
+
+/*
+ * FP32 arithmetic peak of `device`, measured (the denominator of the
+ * degridding roofline: the footprint sum of Section "Implementation" is
+ * bound by FP32 fused multiply-adds).  Runs 8 CTAs of 256 threads per SM,
+ * each thread 16 independent FMA chains, as packed two-wide FFMA2
+ * (packed != 0, the form the degridding kernel issues) or scalar FFMA, and
+ * times 5 launches of about 4 ms after a warm-up one with CUDA events on a
+ * stream of its own.  *tflops receives the best launch's 2 flop per lane FMA
+ * divided by its duration, in TFLOP/s.  Synchronous; allocates and frees
+ * 1.2 MB of device memory.  Returns DG_OK, DG_ERR_ARG (tflops NULL or
+ * device < 0), DG_ERR_OOM or DG_ERR_CUDA.
+ */
+dg_status degrid_measure_fp32_peak(int device, int packed, double *tflops);
 
 /*
  * Degridding (Section "Implementation", the weighted footprint sum):

@@ -26,7 +26,7 @@ from ._native import (DG_C32_BF16, DG_C32_F16, DG_C64, DG_ERR_OFFSETS, DG_OK,  #
                       DegridError, SIGNATURES, check, lib_path, load, status_string)
 
 __all__ = ["DegridPlan", "DegridFn", "DegridError", "pack_subgrids", "degrid", "autotune",
-           "synth", "load", "lib_path", "SIGNATURES"]
+           "measure_fp32_peak", "synth", "load", "lib_path", "SIGNATURES"]
 
 DTYPES = {"c64": DG_C64, "f16": DG_C32_F16, "bf16": DG_C32_BF16}
 
@@ -348,6 +348,15 @@ def pack_subgrids(subgrids, dtype: str, stream=None):
                                      elems, _vp(subgrids), _vp(codes), _vp(scale))
     check(st, "degrid_pack_subgrids")
     return codes, scale
+
+
+def measure_fp32_peak(device: int = 0, packed: bool = True) -> float:
+    """FP32 FMA throughput of `device` in TFLOP/s, measured by
+    degrid_measure_fp32_peak (packed FFMA2 chains, or scalar FFMA)."""
+    out = ctypes.c_double(0.0)
+    check(load().degrid_measure_fp32_peak(int(device), 1 if packed else 0, ctypes.byref(out)),
+          "degrid_measure_fp32_peak")
+    return float(out.value)
 
 
 def degrid(plan: DegridPlan, subgrids, uvw, vis_offsets, scale=None):

@@ -248,9 +248,16 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
     Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const size_t smem = smem_bytes(p);
     auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
+    // the dynamic shared-memory limit is set once per device, instance and size
+    static size_t smem_set[2][kMaxDevices] = {};
+    size_t *set = &smem_set[p->guv2 ? 1 : 0][p->device < kMaxDevices ? p->device : 0];
+    if (p->device >= kMaxDevices || *set != smem) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        if (p->device < kMaxDevices)
+            *set = smem;
+    }
     kernel<<<grid_blocks, p->warps_per_block * kWarp, smem, st>>>(
         p->geo, uvw, reinterpret_cast<const float2 *>(vis_in), p->guv, p->gw, sched,
         reinterpret_cast<float2 *>(sub_out), p->status, p->guv2);

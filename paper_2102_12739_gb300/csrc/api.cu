@@ -89,12 +89,26 @@ void free_plan_buffers(degrid_plan *p)
     cudaFree(p->chunks);
 }
 
-// Grows the schedule scratch so that S subgrids and n_vis visibilities fit.
-// This allocates, so it must not run inside a stream capture: the first call
-// with the largest sizes has to happen before capturing.
-dg_status ensure_capacity(degrid_plan *p, int S, int64_t n_vis)
+// Chunk size of one call: the plan's, halved for small calls until the
+// list makes about two chunks per resident warp (so that a short list still
+// spreads over the GPU), but never below one 64-visibility pipeline step.
+// Results do not depend on it (every visibility's arithmetic is the same).
+int call_chunk(const degrid_plan *p, int64_t n_vis)
 {
-    const int64_t need_chunks = n_vis / p->chunk + S + 1;
+    const int64_t warps = (int64_t)p->sm_count * 16;
+    int c = p->chunk;
+    while (c > 64 && c % 64 == 0 && n_vis / c < 2 * warps)
+        c >>= 1;
+    return c;
+}
+
+// Grows the schedule scratch so that S subgrids and n_vis visibilities fit
+// in chunks of `chunk`.  This allocates, so it must not run inside a stream
+// capture: the first call with the largest sizes has to happen before
+// capturing.
+dg_status ensure_capacity(degrid_plan *p, int S, int64_t n_vis, int chunk)
+{
+    const int64_t need_chunks = n_vis / chunk + S + 1;
     if (need_chunks > 0x7fffffff)
         return DG_ERR_ARG;
     if (S > p->cap_subgrids) {
@@ -143,7 +157,7 @@ struct KernelTimer {
 
 // Persistent grid: the resident CTAs of every SM, but no more CTAs than
 // there are chunks for their chunk-claiming warps.
-int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int max_per_sm, int claimers_per_block)
+int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int chunk, int max_per_sm, int claimers_per_block)
 {
     int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : max_per_sm;
     if (per_sm < 1)
@@ -151,7 +165,7 @@ int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int max_per_sm, int claime
     if (per_sm > max_per_sm)
         per_sm = max_per_sm;
     int64_t blocks = (int64_t)p->sm_count * per_sm;
-    const int64_t max_chunks = n_vis / p->chunk + S;
+    const int64_t max_chunks = n_vis / chunk + S;
     const int64_t useful = (max_chunks + claimers_per_block - 1) / claimers_per_block;
     if (blocks > useful)
         blocks = useful;
@@ -458,18 +472,19 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
     DeviceGuard guard(p->device);
     if (!guard.ok)
         return DG_ERR_CUDA;
-    dg_status st = ensure_capacity(p, n_subgrids, n_vis);
+    const int chunk = call_chunk(p, n_vis);
+    dg_status st = ensure_capacity(p, n_subgrids, n_vis, chunk);
     if (st != DG_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, p->chunk, p->prefix,
+    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, p->prefix,
                                         p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
     if (p->max_blocks_degrid == 0)
         p->max_blocks_degrid = dg_max_blocks_per_sm_degrid(p);
-    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_degrid, p->warps_per_block);
+    const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, p->max_blocks_degrid, p->warps_per_block);
     KernelTimer timer(p, s);
     e = dg_launch_degrid(p, s, subgrids, subgrid_scale, uvw, vis_offsets, vis_out, blocks);
     timer.stop();
@@ -499,17 +514,18 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
     }
     if (n_vis == 0)
         return DG_OK;
-    dg_status st = ensure_capacity(p, n_subgrids, n_vis);
+    const int chunk = call_chunk(p, n_vis);
+    dg_status st = ensure_capacity(p, n_subgrids, n_vis, chunk);
     if (st != DG_OK)
         return st;
-    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, p->chunk, p->prefix,
+    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, p->prefix,
                                         p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
     if (p->max_blocks_adjoint == 0)
         p->max_blocks_adjoint = dg_max_blocks_per_sm_adjoint(p);
-    const int blocks = grid_blocks(p, n_subgrids, n_vis, p->max_blocks_adjoint, p->warps_per_block);
+    const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, p->max_blocks_adjoint, p->warps_per_block);
     KernelTimer timer(p, s);
     e = dg_launch_adjoint(p, s, uvw, vis_offsets, vis_in, sub_out, blocks);
     timer.stop();

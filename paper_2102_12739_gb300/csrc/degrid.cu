@@ -463,10 +463,16 @@ cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const 
 {
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-        return e;
+    // the dynamic shared-memory limit is set once per device and size
+    static size_t smem_set[kMaxDevices] = {};
+    if (p->device >= kMaxDevices || smem_set[p->device] != smem) {
+        cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        if (p->device < kMaxDevices)
+            smem_set[p->device] = smem;
+    }
     // 16-byte footprint loads need an aligned stack and nz a multiple of the
     // elements per 16 bytes
     const bool vec_ok = (reinterpret_cast<uintptr_t>(subgrids) & 15) == 0 &&

@@ -17,6 +17,7 @@ constexpr int kUV = 8;
 constexpr int kW = 4;
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxDevices = 64;     // devices whose per-kernel launch attributes are cached
 
 // Subgrid shape and oversampling, passed by value to every kernel.
 struct Geometry {

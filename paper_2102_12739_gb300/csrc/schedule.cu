@@ -13,6 +13,8 @@
 //   1. chunk_prefix: one block validates vis_offsets and scans
 //      ceil(count_s / chunk) into prefix[S + 1];
 //   2. chunk_fill: writes (s, count, first visibility) for every chunk.
+// For small calls (few subgrids and chunks, bounded on the host) the block of
+// chunk_prefix also writes the chunks, saving a launch.
 #include "internal.cuh"
 
 namespace dg {
@@ -20,10 +22,14 @@ namespace {
 
 constexpr int kScanThreads = 1024;
 
+constexpr int kSmallSubgrids = 32;          // one-launch schedule: at most this many subgrids
+constexpr int kSmallChunks = 8192;          // and at most this many chunks (host bound)
+
 __global__ void __launch_bounds__(kScanThreads)
 chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
              int *__restrict__ prefix, int *__restrict__ n_chunks, int capacity,
-             int *__restrict__ work_counter, DeviceStatus *__restrict__ status)
+             int *__restrict__ work_counter, DeviceStatus *__restrict__ status,
+             ChunkDesc *__restrict__ fill_chunks)
 {
     __shared__ long long warp_sums[kScanThreads / kWarp];
     __shared__ long long carry_sh;
@@ -85,6 +91,18 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
         prefix[S > 0 ? S : 0] = (int)total;
         *n_chunks = (int)total;
     }
+    if (!fill_chunks)
+        return;
+    __syncthreads();                        // prefix[] visible to the whole block
+    for (int s = 0; s < S; ++s) {
+        const int lo = prefix[s], hi = prefix[s + 1];
+        const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
+        for (int k = lo + tid; k < hi; k += kScanThreads) {
+            const int64_t first = vis_lo + (int64_t)(k - lo) * chunk;
+            const int64_t last = min(first + (int64_t)chunk, vis_hi);
+            fill_chunks[k] = ChunkDesc{s, (int)(last - first), (long long)first};
+        }
+    }
 }
 
 __global__ void chunk_fill(const int *__restrict__ prefix, const int64_t *__restrict__ offs,
@@ -108,10 +126,12 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
                             ChunkDesc *chunks, int capacity, int *work_counter,
                             DeviceStatus *status)
 {
+    const bool small = n_subgrids <= kSmallSubgrids && n_vis / chunk + n_subgrids <= kSmallChunks;
     chunk_prefix<<<1, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, prefix,
-                                             n_chunks, capacity, work_counter, status);
+                                             n_chunks, capacity, work_counter, status,
+                                             small ? chunks : nullptr);
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || n_subgrids == 0)
+    if (err != cudaSuccess || n_subgrids == 0 || small)
         return err;
     const int blocks = n_subgrids < 4096 ? n_subgrids : 4096;
     chunk_fill<<<blocks, 256, 0, st>>>(prefix, vis_offsets, n_subgrids, chunk, chunks);
