@@ -333,10 +333,12 @@ def batched_section(torch, dg, synth, dev, flush, steps):
             "autotune_candidates": len(tuned["timings"])}
 
 
-def scatter_section(torch, dg, synth, dev, flush, steps):
+def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
     """Sparse coverage: every visibility has its own footprint (no reuse), the
     regime where subgrid bytes, and so the storage type, matter.  Each storage
-    type is autotuned over the summing arms, then timed."""
+    type is autotuned over the summing arms, then timed.  The no-reuse bound
+    is the footprint bytes (256 elements of 8 B complex64 or 4 B FP16/BF16 per
+    visibility) at the measured L2 read bandwidth."""
     import oracle
     w = synth.workload("scatter16_250k")
     sub_np = w.subgrids()
@@ -360,14 +362,18 @@ def scatter_section(torch, dg, synth, dev, flush, steps):
             s_ms, k_ms = time_steps(torch, plan, step, steps, flush, torch.cuda.current_stream(dev))
             err = sampled_error(out.cpu().numpy(), w, g_uv, g_w, sub_np)
         ms = sorted(s_ms)[len(s_ms) // 2]
+        kms = sorted(k_ms)[len(k_ms) // 2]
+        gather_ms = w.n_vis * 256 * (8 if dt == "c64" else 4) / (l2_gbs * 1e9) * 1e3
         res[dt] = {"value": w.n_vis / (ms * 1e-3), "ms_per_step": ms,
-                   "kernel_ms": sorted(k_ms)[len(k_ms) // 2], "rel_l2": err[0],
+                   "kernel_ms": kms, "l2_gather_bound_ms": gather_ms,
+                   "frac_of_l2_gather_bound": gather_ms / kms, "rel_l2": err[0],
                    "arm": "direct" if tuned["tuning"]["direct_runs"] < 33 else "footprint cache",
                    "tuning": tuned["tuning"]}
         del codes, scale
     return {"workload": "scatter16_250k: 16 subgrids 512x512x4, 250,000 visibilities each "
                         "scattered uniformly over the valid box (no footprint shared by "
-                        "consecutive visibilities)", "unit": UNIT, "steps": steps, "by_storage": res}
+                        "consecutive visibilities)", "unit": UNIT, "steps": steps,
+            "l2_read_gbs_measured": l2_gbs, "by_storage": res}
 
 
 def latency_section(torch, dg, synth, dev, steps):
@@ -395,7 +401,8 @@ def latency_section(torch, dg, synth, dev, steps):
     return {"workload": "line1_20k: 1 subgrid 512x512x4, 20,000 visibilities on one line",
             "call_us": ms[len(ms) // 2] * 1e3, "value": w.n_vis / (ms[len(ms) // 2] * 1e-3),
             "unit": UNIT, "steps": steps,
-            "call_includes": "offset validation and chunk scan, chunk table, degridding kernel"}
+            "call_includes": "one scheduling launch (offset validation, chunk scan and chunk "
+                             "table) and the degridding kernel"}
 
 
 def table2d_section(torch, dg, synth, dev, flush, steps, sub, sub_np, uvw, offs, w):
@@ -620,7 +627,8 @@ def run_ours(args, rank, world):
         # against the FP64 oracle on the original complex64 subgrids (quantisation
         # included) and, for FP16/BF16, on the values the kernel reads (kernel error)
         sweep = {"c64": {"value": value, "kernel_ms": mean_kern, "rel_l2": err_c64[0],
-                         "max_abs": err_c64[1], "compensated": False}}
+                         "max_abs": err_c64[1], "compensated": False,
+                         "roofline_frac": roofline["frac"], "hbm_bound_ms": hbm_ms}}
         for dt in ("c64", "f16", "bf16"):
             if dt == "c64":
                 codes, scale, stored_np = sub, None, None
@@ -644,10 +652,14 @@ def run_ours(args, rank, world):
                     e = sampled_error(o2_np, w, g_uv, g_w, sub_np)
                     ek = sampled_error(o2_np, w, g_uv, g_w, stored_np) if stored_np is not None else e
                 ms = sum(s_ms) / len(s_ms)
+                kms = sum(k_ms) / len(k_ms)
+                elem = 8 if dt == "c64" else 4
                 sweep[dt + ("_compensated" if comp else "")] = {
-                    "value": w.n_vis / (ms * 1e-3), "kernel_ms": sum(k_ms) / len(k_ms),
+                    "value": w.n_vis / (ms * 1e-3), "kernel_ms": kms,
                     "rel_l2": e[0], "max_abs": e[1], "rel_l2_vs_stored_values": ek[0],
-                    "compensated": comp}
+                    "compensated": comp,
+                    "roofline_frac": w.n_vis * FLOP_PER_VIS / (kms * 1e-3) / 1e12 / peak_tflops,
+                    "hbm_bound_ms": (w.n_vis * 32 + touched * elem) / (peaks["hbm_gbs"] * 1e9) * 1e3}
             del codes, scale
         line["precision_sweep"] = sweep
 
@@ -689,7 +701,8 @@ def run_ours(args, rank, world):
                                           uvw, offs, w)
 
     if not args.no_scatter:
-        line["scatter"] = scatter_section(torch, dg, synth, dev, flush, args.aux_steps)
+        line["scatter"] = scatter_section(torch, dg, synth, dev, flush, args.aux_steps,
+                                          dg.measure_l2_read_bw(local))
 
     if not args.no_batched:
         del sub_np

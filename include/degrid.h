@@ -211,6 +211,20 @@ dg_status degrid_plan_kernel_times_ms(degrid_plan_t plan, float *ms_out, int cap
 dg_status degrid_measure_fp32_peak(int device, int packed, double *tflops);
 
 /*
+ * L2-to-SM read bandwidth of `device`, measured (the no-reuse gather bound:
+ * without footprint reuse every visibility reads its own 8 x 8 x 4
+ * footprint, 2 KB in complex64 or 1 KB in FP16/BF16, from L2).  Runs 8 CTAs
+ * of 256 threads per SM that read an L2-resident buffer (8 x 16 bytes per
+ * thread, 39.8 MB on 152 SMs) 1000 times with L1-bypassing 16-byte loads,
+ * and times 5 launches after a warm-up one with CUDA events on a stream of
+ * its own.  *gbs receives the bytes read by the best launch divided by its
+ * duration, in GB/s (1e9 bytes).  Synchronous; allocates and frees the
+ * buffer.  Returns DG_OK, DG_ERR_ARG (gbs NULL or device < 0), DG_ERR_OOM or
+ * DG_ERR_CUDA.
+ */
+dg_status degrid_measure_l2_read_bw(int device, double *gbs);
+
+/*
  * Degridding (Section "Implementation", the weighted footprint sum):
  *   vis_out[i] = sum_{b<8} sum_{a<8} sum_{c<4} g_uv[fv][b] g_uv[fu][a]
  *                g_w[fw][c] * sub[s][y0+b][x0+a][z0+c]

@@ -26,7 +26,7 @@ from ._native import (DG_C32_BF16, DG_C32_F16, DG_C64, DG_ERR_OFFSETS, DG_OK,  #
                       DegridError, SIGNATURES, check, lib_path, load, status_string)
 
 __all__ = ["DegridPlan", "DegridFn", "DegridError", "pack_subgrids", "degrid", "autotune",
-           "measure_fp32_peak", "synth", "load", "lib_path", "SIGNATURES"]
+           "measure_fp32_peak", "measure_l2_read_bw", "synth", "load", "lib_path", "SIGNATURES"]
 
 DTYPES = {"c64": DG_C64, "f16": DG_C32_F16, "bf16": DG_C32_BF16}
 
@@ -356,6 +356,15 @@ def measure_fp32_peak(device: int = 0, packed: bool = True) -> float:
     out = ctypes.c_double(0.0)
     check(load().degrid_measure_fp32_peak(int(device), 1 if packed else 0, ctypes.byref(out)),
           "degrid_measure_fp32_peak")
+    return float(out.value)
+
+
+def measure_l2_read_bw(device: int = 0) -> float:
+    """L2-to-SM read bandwidth of `device` in GB/s, measured by
+    degrid_measure_l2_read_bw."""
+    out = ctypes.c_double(0.0)
+    check(load().degrid_measure_l2_read_bw(int(device), ctypes.byref(out)),
+          "degrid_measure_l2_read_bw")
     return float(out.value)
 
 

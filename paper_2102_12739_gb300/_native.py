@@ -49,6 +49,7 @@ SIGNATURES = {
     "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_get_compensated": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_measure_fp32_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "degrid_measure_l2_read_bw": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_plan_enable_timing": (_I, [_P, _I]),
     "degrid_plan_kernel_times_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I,
                                          ctypes.POINTER(_I)]),

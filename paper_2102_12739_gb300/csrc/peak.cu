@@ -1,10 +1,15 @@
-// FP32 arithmetic peak of the device, measured: the denominator of the
-// degridding kernel's roofline.  The footprint sum is bound by FP32
-// fused multiply-adds (256 complex x real products per visibility, Section
-// "Implementation"), so its roofline is the rate at which the SMs retire
-// them.  This kernel fills every SM with independent FMA chains, scalar
-// (FFMA) or packed two-wide (FFMA2, the form the degridding kernel issues),
-// and the host times it with CUDA events.
+// Device peaks measured on the GPU, the denominators of the degridding
+// roofline and its diagnostics.
+//  * FP32 FMA rate: the footprint sum is bound by FP32 fused multiply-adds
+//    (256 complex x real products per visibility, Section "Implementation"),
+//    so its roofline is the rate at which the SMs retire them.  A kernel
+//    fills every SM with independent FMA chains, scalar (FFMA) or packed
+//    two-wide (FFMA2, the form the degridding kernel issues).
+//  * L2 read bandwidth: without footprint reuse every visibility gathers its
+//    own 8 x 8 x 4 footprint (2 KB complex64, 1 KB FP16/BF16) from L2.  A
+//    kernel streams an L2-resident buffer into every SM with L1-bypassing
+//    16-byte loads.
+// The host times both with CUDA events (best of 5 launches after a warm-up).
 #include "internal.cuh"
 
 namespace dg {
@@ -58,6 +63,60 @@ fp32_peak_kernel(int iters, float m, float a, float *__restrict__ out)
     out[t] = sum;
 }
 
+constexpr int kL2PerThread = 8;             // 16-byte loads per thread per pass
+
+// Reads buf[0, n4) `passes` times, grid-strided, bypassing L1; the xor of
+// everything read is stored so that no load is dead.
+__global__ void __launch_bounds__(kPeakThreads)
+l2_read_kernel(const uint4 *__restrict__ buf, long long n4, int passes, unsigned *__restrict__ out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned acc = 0;
+    for (int p = 0; p < passes; ++p) {
+#pragma unroll 4
+        for (long long i = t; i < n4; i += stride) {
+            const uint4 x = __ldcg(buf + i);
+            acc ^= x.x ^ x.y ^ x.z ^ x.w;
+        }
+    }
+    out[t] = acc;
+}
+
+// Times `launch` (a callable issuing one launch on `st`): best of 5 after a
+// warm-up; returns the best duration in ms (0 on error, with *err set).
+template <class F>
+float best_of_5(cudaStream_t st, F launch, cudaError_t *err)
+{
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t1);
+    float best = 0.0f;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {   // launch 0 warms up
+        e = cudaEventRecord(t0, st);
+        if (e == cudaSuccess) {
+            launch();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaEventRecord(t1, st);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(t1);
+        float ms = 0.0f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && rep > 0 && ms > 0.0f && (best == 0.0f || ms < best))
+            best = ms;
+    }
+    if (t0)
+        cudaEventDestroy(t0);
+    if (t1)
+        cudaEventDestroy(t1);
+    *err = e;
+    return best;
+}
+
 }  // namespace
 }  // namespace dg
 
@@ -76,48 +135,69 @@ extern "C" dg_status degrid_measure_fp32_peak(int device, int packed, double *tf
     const long long threads = (long long)blocks * kPeakThreads;
     float *out = nullptr;
     cudaStream_t st = nullptr;
-    cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess)
         e = cudaMalloc(&out, sizeof(float) * (size_t)threads);
     if (e == cudaSuccess)
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaEventCreate(&t0);
-    if (e == cudaSuccess)
-        e = cudaEventCreate(&t1);
     // 2 flop per lane FMA; 2 lanes per FFMA2 or two scalar chains per pair
     const int iters = 2048;                 // about 4 ms per launch at 80 TFLOP/s
     const double flop = (double)threads * iters * kUnroll * kChains * 2 * 2;
     float best = 0.0f;
-    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {   // launch 0 warms up
-        e = cudaEventRecord(t0, st);
-        if (e == cudaSuccess) {
+    if (e == cudaSuccess)
+        best = best_of_5(st, [&] {
             if (packed)
                 fp32_peak_kernel<true><<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999999f, 1e-7f, out);
             else
                 fp32_peak_kernel<false><<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999999f, 1e-7f, out);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess)
-            e = cudaEventRecord(t1, st);
-        if (e == cudaSuccess)
-            e = cudaEventSynchronize(t1);
-        float ms = 0.0f;
-        if (e == cudaSuccess)
-            e = cudaEventElapsedTime(&ms, t0, t1);
-        if (e == cudaSuccess && rep > 0 && ms > 0.0f && (best == 0.0f || ms < best))
-            best = ms;
-    }
-    if (t0)
-        cudaEventDestroy(t0);
-    if (t1)
-        cudaEventDestroy(t1);
+        }, &e);
     if (st)
         cudaStreamDestroy(st);
     cudaFree(out);
     cudaSetDevice(prev);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess || best <= 0.0f)
         return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
     *tflops = flop / (best * 1e-3) / 1e12;
+    return DG_OK;
+}
+
+extern "C" dg_status degrid_measure_l2_read_bw(int device, double *gbs)
+{
+    using namespace dg;
+    if (!gbs || device < 0)
+        return DG_ERR_ARG;
+    *gbs = 0.0;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
+        return DG_ERR_CUDA;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int blocks = sms * kPeakBlocksPerSM;
+    const long long threads = (long long)blocks * kPeakThreads;
+    const long long n4 = threads * kL2PerThread;           // 39.8 MB on 152 SMs: L2-resident
+    const int passes = 1000;
+    uint4 *buf = nullptr;
+    unsigned *out = nullptr;
+    cudaStream_t st = nullptr;
+    if (e == cudaSuccess)
+        e = cudaMalloc(&buf, sizeof(uint4) * (size_t)n4);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&out, sizeof(unsigned) * (size_t)threads);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(buf, 1, sizeof(uint4) * (size_t)n4, st);
+    float best = 0.0f;
+    if (e == cudaSuccess)
+        best = best_of_5(st, [&] {
+            l2_read_kernel<<<blocks, kPeakThreads, 0, st>>>(buf, n4, passes, out);
+        }, &e);
+    if (st)
+        cudaStreamDestroy(st);
+    cudaFree(out);
+    cudaFree(buf);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess || best <= 0.0f)
+        return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+    *gbs = (double)passes * (double)n4 * sizeof(uint4) / (best * 1e-3) / 1e9;
     return DG_OK;
 }

@@ -1,7 +1,9 @@
-"""The measured FP32 peak (the degridding roofline's denominator) is
-plausible: below the unit-count bound at the maximum SM clock, and not far
-below it (a kernel that did less work than it counts would read above the
-bound; one that failed to fill the SMs would read far below it)."""
+"""The measured device peaks are plausible.  The FP32 peak (the degridding
+roofline's denominator) lies below the unit-count bound at the maximum SM
+clock and not far below it: a kernel that did less work than it counts would
+read above the bound, one that failed to fill the SMs far below it.  The L2
+read bandwidth lies above the HBM copy rate (the buffer is L2-resident) and
+below what the SMs' load paths could take in (128 bytes per SM per clock)."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -27,3 +29,14 @@ def test_measured_fp32_peak_is_within_the_unit_count_bound():
 def test_measure_fp32_peak_rejects_bad_arguments():
     with pytest.raises(dg.DegridError):
         dg.measure_fp32_peak(-1)
+
+
+def test_measured_l2_read_bandwidth_is_between_hbm_and_the_load_path_bound():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    upper = sms * 128 * MAX_SM_MHZ * 1e6 / 1e9
+    bw = dg.measure_l2_read_bw(0)
+    assert 7000.0 < bw <= upper, (bw, upper)
+    with pytest.raises(dg.DegridError):
+        dg.measure_l2_read_bw(-1)
