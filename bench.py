@@ -347,7 +347,8 @@ def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
     offs = torch.from_numpy(w.vis_offsets).to(dev)
     out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
     g_uv, g_w = synth.default_tables()
-    cands = [(256, 8, 0, 33), (256, 8, 0, 9), (512, 4, 0, 33), (512, 4, 0, 9)]
+    cands = [(256, 8, 0, 33, 0), (256, 8, 0, 9, 0), (512, 4, 0, 33, 0), (512, 4, 0, 9, 0),
+             (128, 8, 0, 33, 1), (256, 8, 0, 33, 1), (512, 8, 0, 33, 1)]
     res = {}
     for dt in ("c64", "f16", "bf16"):
         codes, scale = (sub, None) if dt == "c64" else dg.pack_subgrids(sub, dt)
@@ -367,7 +368,8 @@ def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
         res[dt] = {"value": w.n_vis / (ms * 1e-3), "ms_per_step": ms,
                    "kernel_ms": kms, "l2_gather_bound_ms": gather_ms,
                    "frac_of_l2_gather_bound": gather_ms / kms, "rel_l2": err[0],
-                   "arm": "direct" if tuned["tuning"]["direct_runs"] < 33 else "footprint cache",
+                   "arm": ("gather" if tuned["tuning"]["gather"] else
+                           "direct" if tuned["tuning"]["direct_runs"] < 33 else "footprint cache"),
                    "tuning": tuned["tuning"]}
         del codes, scale
     return {"workload": "scatter16_250k: 16 subgrids 512x512x4, 250,000 visibilities each "

@@ -59,7 +59,8 @@ typedef enum {
     DG_ERR_DTYPE = 4,          /* storage type not supported / scale missing */
     DG_ERR_OFFSETS = 5,        /* vis_offsets malformed (found on the device) */
     DG_ERR_UNSUPPORTED = 6,    /* GCF support / subgrid shape not supported */
-    DG_ERR_SCRATCH_LIMIT = 7   /* sizes exceed the fixed scratch of degrid_execute_noalloc */
+    DG_ERR_SCRATCH_LIMIT = 7,  /* sizes exceed the fixed scratch of degrid_execute_noalloc */
+    DG_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up (found on the device) */
 } dg_status;
 
 /* Subgrid storage: complex64, or FP16 / BF16 (re, im) pairs with one FP32
@@ -99,8 +100,6 @@ dg_status degrid_plan_create(degrid_plan_t *out, int nx, int ny, int nz,
                              const double *g_w, int w_support, int w_oversample,
                              dg_dtype dtype, int device);
 
-/* Release the plan and every device buffer it owns.  Synchronises the
- * plan's device first.  NULL is ignored. */
 /*
  * Create a plan with a non-separable G_uv (the paper states G_uv as a kernel
  * of support 8 x 8, Section "Implementation"; degrid_plan_create takes the
@@ -120,6 +119,8 @@ dg_status degrid_plan_create_2d(degrid_plan_t *out, int nx, int ny, int nz, cons
                                 int uv_oversample, const double *g_w, int w_support,
                                 int w_oversample, dg_dtype dtype, int device);
 
+/* Release the plan and every device buffer it owns.  Synchronises the
+ * plan's device first.  NULL is ignored. */
 void degrid_plan_destroy(degrid_plan_t plan);
 
 /*
@@ -173,6 +174,26 @@ dg_status degrid_plan_get_compensated(degrid_plan_t plan, int *enabled);
 #define DG_DIRECT_RUNS_SHORT 9
 dg_status degrid_plan_set_direct_runs(degrid_plan_t plan, int min_runs);
 dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
+
+/*
+ * Gather arm for sparse coverage (lists whose consecutive visibilities
+ * rarely share a footprint: the short-list regime of the paper's kernels
+ * D2/D4, Section "Results").  With enabled = 1, degrid_execute streams every
+ * visibility's own 8 x 8 x 4 footprint into shared memory with asynchronous
+ * copies, several footprints in flight per warp, instead of caching the
+ * footprint sum M per run; a separate kernel with one CTA per SM (8 warps
+ * for complex64, 16 for FP16/BF16), so the warps_per_block and
+ * blocks_per_sm of the tuning do not apply to it (the chunk size does).
+ * Same arithmetic in the same order as the footprint-cache path: results
+ * are bitwise identical; the compensated setting applies.  Only the speed
+ * differs: it wins when footprints are scattered and loses on dense lists,
+ * where one cached M serves hundreds of visibilities.  Needs nz = 4 and a
+ * separable G_uv table: enabling it on another plan returns
+ * DG_ERR_UNSUPPORTED.  Returns DG_OK, DG_ERR_ARG (enabled not 0 / 1) or
+ * DG_ERR_UNSUPPORTED.
+ */
+dg_status degrid_plan_set_gather(degrid_plan_t plan, int enabled);
+dg_status degrid_plan_get_gather(degrid_plan_t plan, int *enabled);
 
 /* Read back the current tuning (any pointer may be NULL). */
 dg_status degrid_plan_get_tuning(degrid_plan_t plan, int *chunk, int *warps_per_block,
@@ -320,8 +341,10 @@ dg_status degrid_pack_subgrids(void *stream, dg_dtype dtype, int n_subgrids, int
 /*
  * Read and clear the device-side status of the plan: synchronises `stream`,
  * stores the number of invalid visibilities seen since the last call in
- * *n_invalid (may be NULL) and returns DG_ERR_OFFSETS if a call saw
- * malformed vis_offsets, else DG_OK (or DG_ERR_CUDA).
+ * *n_invalid (may be NULL) and returns DG_ERR_TIMEOUT if a bounded wait of
+ * a kernel gave up (the gather kernel's waits on its copies; the results of
+ * that call are incomplete), else DG_ERR_OFFSETS if a call saw malformed
+ * vis_offsets, else DG_OK (or DG_ERR_CUDA).
  */
 dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid);
 

@@ -74,7 +74,7 @@ class DegridPlan:
     """
 
     def __init__(self, shape=synth.SUBGRID_SHAPE, g_uv=None, g_w=None, dtype: str = "c64",
-                 device=None, compensated: bool = False, g_uv2=None):
+                 device=None, compensated: bool = False, g_uv2=None, gather: bool = False):
         torch = _torch()
         lib = load()
         if dtype not in DTYPES:
@@ -121,6 +121,8 @@ class DegridPlan:
         self._h = h
         if compensated:
             self.set_compensated(True)
+        if gather:
+            self.set_gather(True)
 
     # -- lifetime --------------------------------------------------------
     @property
@@ -156,7 +158,7 @@ class DegridPlan:
         check(load().degrid_plan_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(w),
                                             ctypes.byref(b)), "degrid_plan_get_tuning")
         return {"chunk": c.value, "warps_per_block": w.value, "blocks_per_sm": b.value,
-                "direct_runs": self.direct_runs}
+                "direct_runs": self.direct_runs, "gather": self.gather}
 
     def set_compensated(self, enabled: bool = True) -> None:
         """Compensated (TwoSum) reduction of the lane partials in degrid()."""
@@ -183,6 +185,19 @@ class DegridPlan:
         check(load().degrid_plan_get_direct_runs(self.handle, ctypes.byref(v)),
               "degrid_plan_get_direct_runs")
         return v.value
+
+    def set_gather(self, enabled: bool = True) -> None:
+        """Sum through the gather kernel (every footprint streamed into shared
+        memory; for scattered coverage).  Results are bitwise the same as the
+        footprint-cache path.  Needs nz = 4 and a separable G_uv table."""
+        check(load().degrid_plan_set_gather(self.handle, 1 if enabled else 0),
+              "degrid_plan_set_gather")
+
+    @property
+    def gather(self) -> bool:
+        v = ctypes.c_int()
+        check(load().degrid_plan_get_gather(self.handle, ctypes.byref(v)), "degrid_plan_get_gather")
+        return bool(v.value)
 
     def enable_timing(self, n_slots: int = 4096) -> None:
         """Record a CUDA event pair around the main kernel of each of the next

@@ -21,6 +21,7 @@ DG_ERR_DTYPE = 4
 DG_ERR_OFFSETS = 5
 DG_ERR_UNSUPPORTED = 6
 DG_ERR_SCRATCH_LIMIT = 7
+DG_ERR_TIMEOUT = 8
 
 DG_C64 = 0
 DG_C32_F16 = 1
@@ -48,6 +49,8 @@ SIGNATURES = {
     "degrid_plan_set_direct_runs": (_I, [_P, _I]),
     "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_get_compensated": (_I, [_P, ctypes.POINTER(_I)]),
+    "degrid_plan_set_gather": (_I, [_P, _I]),
+    "degrid_plan_get_gather": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_measure_fp32_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_measure_l2_read_bw": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_plan_enable_timing": (_I, [_P, _I]),

@@ -187,6 +187,7 @@ const char *degrid_status_string(dg_status status)
     case DG_ERR_OFFSETS: return "malformed vis_offsets";
     case DG_ERR_UNSUPPORTED: return "unsupported GCF support or subgrid shape";
     case DG_ERR_SCRATCH_LIMIT: return "sizes exceed the fixed scratch of degrid_execute_noalloc";
+    case DG_ERR_TIMEOUT: return "a bounded device-side wait gave up; results are incomplete";
     }
     return "unknown status";
 }
@@ -370,6 +371,24 @@ dg_status degrid_plan_set_direct_runs(degrid_plan_t p, int min_runs)
     return DG_OK;
 }
 
+dg_status degrid_plan_set_gather(degrid_plan_t p, int enabled)
+{
+    if (!p || (enabled != 0 && enabled != 1))
+        return DG_ERR_ARG;
+    if (enabled && !dg_gather_supported(p))
+        return DG_ERR_UNSUPPORTED;
+    p->gather = enabled;
+    return DG_OK;
+}
+
+dg_status degrid_plan_get_gather(degrid_plan_t p, int *enabled)
+{
+    if (!p || !enabled)
+        return DG_ERR_ARG;
+    *enabled = p->gather;
+    return DG_OK;
+}
+
 dg_status degrid_plan_get_direct_runs(degrid_plan_t p, int *min_runs)
 {
     if (!p || !min_runs)
@@ -482,6 +501,14 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
+    if (p->gather) {
+        // one CTA per SM
+        const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, 1, dg_gather_warps(p->dtype));
+        KernelTimer timer(p, s);
+        e = dg_launch_gather(p, s, subgrids, n_subgrids, subgrid_scale, uvw, vis_out, blocks);
+        timer.stop();
+        return from_cuda(e);
+    }
     if (p->max_blocks_degrid == 0)
         p->max_blocks_degrid = dg_max_blocks_per_sm_degrid(p);
     const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, p->max_blocks_degrid, p->warps_per_block);
@@ -587,6 +614,8 @@ dg_status degrid_get_status(degrid_plan_t p, void *stream, int64_t *n_invalid)
         return from_cuda(e);
     if (n_invalid)
         *n_invalid = (int64_t)h.n_invalid;
+    if (h.flags & dg::kFlagTimeout)
+        return DG_ERR_TIMEOUT;
     return (h.flags & (dg::kFlagOffsets | dg::kFlagCapacity)) ? DG_ERR_OFFSETS : DG_OK;
 }
 

@@ -213,6 +213,7 @@ struct degrid_plan {
     int blocks_per_sm;
     int compensated;            // compensated (TwoSum) reduction of the lane partials
     int direct_runs;            // non-uniform halves with at least this many runs take the direct sum
+    int gather;                 // sum through the gather kernel (gather.cu)
     int max_blocks_degrid;      // occupancy results, 0 = not computed yet
     int max_blocks_adjoint;
     struct dg_host_exec *hostx; // streams and staging of degrid_execute_host (host_exec.cu), lazily
@@ -232,6 +233,10 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
                               float *sub_out, int grid_blocks);
 cudaError_t dg_launch_coords(degrid_plan *p, cudaStream_t st, const double *uvw,
                              int64_t n_vis, int32_t *coords_out);
+cudaError_t dg_launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids, int n_subgrids,
+                             const float *scale, const double *uvw, float *vis_out, int grid_blocks);
+int dg_gather_warps(dg_dtype dtype);            // warps per CTA of the gather kernel
+bool dg_gather_supported(const degrid_plan *p);
 int dg_max_blocks_per_sm_degrid(degrid_plan *p);
 int dg_max_warps_per_block();        // largest warps_per_block the kernels are built for
 int dg_max_blocks_per_sm_adjoint(degrid_plan *p);

@@ -4,9 +4,11 @@ The paper picks N_b, the visibilities per thread block, by hand and finds
 that the best value depends on the step du, dv, dw while N_b = 32 is good
 enough, and it switches between kernel variants by list length (Section
 "Results").  Here the knobs are the chunk size (visibilities per work item),
-warps per CTA, resident CTAs per SM and the summing arm (footprint cache only,
-or the direct per-visibility arm for halves with many short runs, which wins
-when footprints overlap but their w rows change often); this module times a
+warps per CTA, resident CTAs per SM and the summing arm (footprint cache only;
+the direct per-visibility arm for halves with many short runs, which wins
+when footprints overlap but their w rows change often; or the gather kernel,
+which streams every footprint through shared memory and wins when footprints
+are scattered); this module times a
 small grid of candidates on the caller's own inputs with CUDA events and
 keeps the fastest on the plan.  Results are cached in a JSON file
 keyed by GPU name, storage type and a coarse description of the inputs, so a
@@ -27,18 +29,19 @@ NEVER = 33          # DG_DIRECT_RUNS_NEVER
 SHORT = 9           # DG_DIRECT_RUNS_SHORT
 
 DEFAULT_CANDIDATES = [
-    (chunk, warps, 0, direct)
+    (chunk, warps, 0, direct, 0)
     for chunk in (128, 256, 512, 1024)
     for warps in (4, 8)
     for direct in (NEVER, SHORT)
-]
+] + [(chunk, 8, 0, NEVER, 1) for chunk in (128, 256, 512)]
 
-_KEYS = ("chunk", "warps_per_block", "blocks_per_sm", "direct_runs")
+_KEYS = ("chunk", "warps_per_block", "blocks_per_sm", "direct_runs", "gather")
 
 
 def _apply(plan, t: dict) -> None:
     plan.set_tuning(t["chunk"], t["warps_per_block"], t["blocks_per_sm"])
     plan.set_direct_runs(t.get("direct_runs", NEVER))
+    plan.set_gather(bool(t.get("gather", 0)))
 
 
 def _cache_path() -> str:
@@ -78,8 +81,10 @@ def cache_key(plan, n_subgrids: int, n_vis: int) -> str:
 
 def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
              candidates: Optional[Iterable] = None, iters: int = 5, use_cache: bool = True):
-    """Time `candidates` (chunk, warps_per_block, blocks_per_sm[, direct_runs])
-    and keep the best; a candidate without direct_runs keeps the plan's.
+    """Time `candidates` (chunk, warps_per_block, blocks_per_sm[, direct_runs[,
+    gather]]) and keep the best; a candidate without direct_runs or gather
+    keeps the plan's.  Candidates the plan cannot run (the gather kernel on a
+    plan with a 2D table) are skipped.
 
     Returns {"tuning": {...}, "ms": best median kernel ms, "timings": [...]}.
     """
@@ -101,9 +106,10 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
         for cand in cands:
             chunk, warps, bps = cand[:3]
             direct = cand[3] if len(cand) > 3 else plan.direct_runs
+            gather = int(cand[4]) if len(cand) > 4 else int(plan.gather)
             try:
                 _apply(plan, {"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
-                              "direct_runs": direct})
+                              "direct_runs": direct, "gather": gather})
             except Exception:
                 continue
             for _ in range(2):                      # warm-up (also sizes scratch)
@@ -112,7 +118,7 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
                 plan.degrid(subgrids, uvw, vis_offsets, scale=scale, out=out)
             ms = sorted(plan.kernel_times_ms(iters))
             timings.append({"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
-                            "direct_runs": direct, "ms": ms[len(ms) // 2]})
+                            "direct_runs": direct, "gather": gather, "ms": ms[len(ms) // 2]})
     finally:
         plan.enable_timing(0)
     if not timings:
