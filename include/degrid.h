@@ -181,8 +181,8 @@ dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
  * D2/D4, Section "Results").  With enabled = 1, degrid_execute streams every
  * visibility's own 8 x 8 x 4 footprint into shared memory with asynchronous
  * copies, several footprints in flight per warp, instead of caching the
- * footprint sum M per run; a separate kernel with one CTA per SM (8 warps
- * for complex64, 16 for FP16/BF16), so the warps_per_block and
+ * footprint sum M per run; a separate kernel with one CTA per SM (12 warps
+ * for complex64, 22 for FP16/BF16), so the warps_per_block and
  * blocks_per_sm of the tuning do not apply to it (the chunk size does).
  * Same arithmetic in the same order as the footprint-cache path: results
  * are bitwise identical; the compensated setting applies.  Only the speed

@@ -8,14 +8,18 @@
 // one footprint at a time per warp, with the loads in registers; here the
 // footprints travel by TMA (one tensor copy per footprint: a box of 8 rows of
 // the stack, each row the 32 elements of the footprint plus 16 bytes) into
-// shared memory, completing on an mbarrier per slot, so a warp keeps two
-// stages of four footprints in flight while it sums a third, and the copy of
-// a stage costs the warp one instruction.  (One bulk copy per 256-byte row
-// ran slower: the copy engine's per-request cost, not bytes, bounded it.)
+// shared memory, completing on an mbarrier per slot: a warp copies the next
+// stage of four footprints while it sums the current one, and the copy of a
+// stage costs it one instruction.  The rate is bytes in flight over L2
+// latency, and shared memory bounds the bytes: the CTA holds as many warps
+// as their two slots each fit (12 for complex64, 22 for FP16/BF16), which
+// measured faster than fewer warps with three or four slots each.  (One bulk
+// copy per 256-byte row ran slower: the copy engine's per-request cost, not
+// bytes, bounded it.)
 //
 // A warp walks chunks in batches of 32 visibilities (lane i snaps visibility
 // i of the batch, as in the other kernels) and each batch in stages of four:
-//   issue:   lane v starts the tensor copy of visibility v of stage n + 2,
+//   issue:   lane v starts the tensor copy of visibility v of stage n + 1,
 //            sixteen lanes copy the g_u and g_v rows (cp.async);
 //   sum:     stage n, lane 8v + b: row b of visibility v,
 //            R_b = sum_a g_u[a] sum_c g_w[c] s[b][a][c];
@@ -43,15 +47,25 @@
 namespace dg {
 namespace {
 
+#ifndef DG_GATHER_STAGES
+#define DG_GATHER_STAGES 2          // slots per warp: stages in flight while one is summed, plus one
+#endif
+#ifndef DG_GATHER_WARPS_C64
+#define DG_GATHER_WARPS_C64 12      // warps per CTA (one CTA per SM), complex64 storage
+#endif
+#ifndef DG_GATHER_WARPS_16
+#define DG_GATHER_WARPS_16 22       // warps per CTA, FP16 / BF16 storage
+#endif
+
 constexpr int kGVis = 4;            // visibilities per stage (8 lanes each)
-constexpr int kGStages = 3;         // slots per warp: two stages in flight while one is summed
+constexpr int kGStages = DG_GATHER_STAGES;
 
 template <int DT>
 struct GatherShape {
     static constexpr int kRowBytes = kUV * kW * Storage<DT>::kBytes;     // one footprint row: 256 / 128
     static constexpr int kPitch = kRowBytes + 16;                        // box row in shared memory
     static constexpr int kBoxX = kPitch / Storage<DT>::kBytes;           // box width, elements: 34 / 36
-    static constexpr int kWarps = DT == DG_C64 ? 8 : 12;                 // per CTA (one CTA per SM)
+    static constexpr int kWarps = DT == DG_C64 ? DG_GATHER_WARPS_C64 : DG_GATHER_WARPS_16;
 };
 
 template <int DT>
@@ -323,7 +337,7 @@ degrid_gather_kernel(const Geometry g, const __grid_constant__ CUtensorMap tmap,
         issued += issue_stage<DT>(is, slots[k], cl, &tmap, guv, uvw, g, status, lane);
     int done = 0;
     for (; done < issued; ++done) {
-        // the slot summed in the previous iteration takes stage done + 2
+        // the slot summed in the previous iteration takes stage done + kGStages - 1
         issued += issue_stage<DT>(is, slots[(done + kGStages - 1) % kGStages], cl, &tmap, guv, uvw, g,
                                   status, lane);
         GatherSlot<DT> &sl = slots[done % kGStages];
