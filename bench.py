@@ -463,10 +463,48 @@ def adjoint_section(torch, dg, synth, dev, flush, steps):
         call_ms = sorted(a.elapsed_time(b) for a, b in ev)
         kern_ms = sorted(plan.kernel_times_ms(steps))
         assert plan.status() == 0
+        # the same workload forward (degridding) and as one autograd step:
+        # forward, loss ||D s - y||^2, backward (gridding of 2 (D s - y))
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        sub = torch.randn((w.n_subgrids,) + w.shape + (2,), generator=gen, device=dev,
+                          dtype=torch.float32).view(torch.complex64)[..., 0].contiguous()
+        vis = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
+
+        def fwd():
+            plan.degrid(sub, uvw, offs, out=vis)
+
+        s_req = sub.clone().requires_grad_(True)
+
+        def train_step():
+            s_req.grad = None
+            v = dg.DegridFn.apply(s_req, uvw, offs, plan)
+            (v - y).abs().pow(2).sum().backward()
+
+        def time_fn(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            for a, b in evs:
+                flush.zero_()
+                a.record(stream)
+                fn()
+                b.record(stream)
+            torch.cuda.synchronize()
+            t = sorted(a.elapsed_time(b) for a, b in evs)
+            return t[len(t) // 2]
+        fwd_ms = time_fn(fwd)
+        step_ms = time_fn(train_step)
+        assert plan.status() == 0
     return {"workload": "diff32_100k: 32 subgrids 512x512x4, 100,000 random-line visibilities each",
             "value": w.n_vis / (call_ms[len(call_ms) // 2] * 1e-3), "unit": "gridded visibilities/s",
             "ms_per_call": call_ms[len(call_ms) // 2], "kernel_ms": kern_ms[len(kern_ms) // 2],
             "call_includes": "zeroing the 256 MB output stack, scheduling kernels, gridding kernel",
+            "forward_ms": fwd_ms, "forward_value": w.n_vis / (fwd_ms * 1e-3),
+            "autograd_step_ms": step_ms,
+            "autograd_step": "DegridFn forward, loss ||D s - y||^2 in torch, backward = gridding",
             "steps": steps}
 
 

@@ -589,3 +589,50 @@ def test_adjoint_dense_lines_full_size_sampled(plan):
         lo, hi = w.vis_offsets[s], w.vis_offsets[s + 1]
         ref, _ = oracle.grid(G_UV, G_W, SHAPE, 1, w.uvw[lo:hi], [0, hi - lo], y[lo:hi])
         assert rel_l2(g[s].cpu().numpy(), ref[0]) <= TOL["c64"]
+
+
+def test_diff32_gradient_matches_central_differences():
+    # 32 subgrids x 100,000 random-line visibilities, L = ||D s - y||^2: the
+    # autograd gradient (the gridding kernel on 2 (D s - y)) against central
+    # differences of L, taken with the degridding kernel, on 64 entries that
+    # footprints touch (real and imaginary parts).  L is quadratic, so the
+    # differences are exact up to rounding for any step.
+    d = dev()
+    w = synth.workload("diff32_100k")
+    sub = torch.from_numpy(w.subgrids()).to(d)
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    y = torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(d)
+    y128 = y.to(torch.complex128)
+    with dg.DegridPlan(device=d) as p:
+        s_req = sub.clone().requires_grad_(True)
+        vis = dg.DegridFn.apply(s_req, uvw, offs, p)
+        (vis - y).abs().pow(2).sum().backward()
+        grad = s_req.grad.cpu().numpy()
+
+        def loss(s):
+            r = p.degrid(s, uvw, offs).to(torch.complex128) - y128
+            return float((r.real ** 2 + r.imag ** 2).sum())
+
+        rng = np.random.default_rng(29)
+        picks = rng.choice(w.n_vis, 64, replace=False)
+        cs, _ = oracle.coords(w.uvw[picks], SHAPE)
+        s_of = np.searchsorted(w.vis_offsets, picks, side="right") - 1
+        h = 0.5
+        worst = 0.0
+        for k, (i, s) in enumerate(zip(picks, s_of)):
+            x0, y0, z0 = cs[k, 0], cs[k, 1], cs[k, 2]
+            idx = (int(s), int(y0 + rng.integers(8)), int(x0 + rng.integers(8)), int(z0 + rng.integers(4)))
+            step = h if k % 2 == 0 else 1j * h
+            orig = sub[idx].item()
+            sub[idx] = orig + step
+            lp = loss(sub)
+            sub[idx] = orig - step
+            lm = loss(sub)
+            sub[idx] = orig
+            fd = (lp - lm) / (2 * h)
+            g = grad[idx].real if k % 2 == 0 else grad[idx].imag
+            scale = max(abs(g), 1e-3 * float(np.sqrt(np.mean(np.abs(grad) ** 2))))
+            worst = max(worst, abs(fd - g) / scale)
+        assert p.status() == 0
+    assert worst <= 1e-3, worst
