@@ -275,19 +275,29 @@ dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
 
 /*
  * degrid_execute with the inputs and the output in HOST memory (no
- * counterpart in the paper, which starts from data on the GPU).  The call
- * copies the subgrids, coordinates and offsets to the device, degrids and
- * copies the visibilities back, overlapping the copies with the sums: the
- * stack is processed in groups of consecutive subgrids (about 64 MB of
- * subgrid data each) through two device slots, with the copy-in of one group,
- * the sums of the previous one and the copy-out of the one before that on
- * three streams of the plan.  Groups without visibilities are not copied.
- * It returns when vis_out is complete (synchronous; the plan's streams are
- * not the caller's).
+ * counterpart in the paper, which starts from data on the GPU), in one of two
+ * ways:
+ *  - in place, when subgrids, uvw and vis_out are page-locked (pinned: mapped
+ *    into the GPU's address space) and the plan allows it (the default, see
+ *    degrid_plan_set_host_direct) and does not use the gather kernel: the
+ *    kernel reads the coordinates and the footprint rows it needs directly
+ *    from host memory over the host link and writes the visibilities there;
+ *    only vis_offsets (and the scales, if not pinned) are copied.  A dense
+ *    list reads a small part of its subgrid, so this moves far fewer bytes
+ *    than copying the stack;
+ *  - otherwise by copies: the subgrids, coordinates and offsets go to the
+ *    device and the visibilities come back, overlapping the copies with the
+ *    sums: the stack is processed in groups of consecutive subgrids (about
+ *    64 MB of subgrid data each) through two device slots, with the copy-in
+ *    of one group, the sums of the previous one and the copy-out of the one
+ *    before that on three streams of the plan.  Groups without visibilities
+ *    are not copied.
+ * Both give the results of degrid_execute bit for bit.  The call returns when
+ * vis_out is complete (synchronous; the plan's streams are not the caller's).
  *   subgrids, subgrid_scale, uvw, vis_offsets, vis_out   HOST pointers, the
- *                  layouts of degrid_execute; page-locked (pinned) memory
- *                  gives full copy bandwidth and overlap, pageable memory
- *                  works at lower speed
+ *                  layouts of degrid_execute; pinned memory gives the in-place
+ *                  form (or full copy bandwidth and overlap), pageable memory
+ *                  works by copies at lower speed
  * vis_offsets is checked on the host: DG_ERR_OFFSETS if vis_offsets[0] != 0,
  * vis_offsets[S] != n_vis or it decreases.  The first call allocates the
  * plan's streams and two staging slots (grown when a later call needs more);
@@ -298,6 +308,14 @@ dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
 dg_status degrid_execute_host(degrid_plan_t plan, int n_subgrids, const void *subgrids,
                               const float *subgrid_scale, const double *uvw,
                               const int64_t *vis_offsets, int64_t n_vis, float *vis_out);
+
+/*
+ * Whether degrid_execute_host may read page-locked host inputs in place
+ * (enabled = 1, the default) or always copies them (0).  Returns DG_OK or
+ * DG_ERR_ARG.
+ */
+dg_status degrid_plan_set_host_direct(degrid_plan_t plan, int enabled);
+dg_status degrid_plan_get_host_direct(degrid_plan_t plan, int *enabled);
 
 /*
  * Adjoint of degrid_execute (gridding): for every visibility i of subgrid s

@@ -193,6 +193,19 @@ class DegridPlan:
         check(load().degrid_plan_set_gather(self.handle, 1 if enabled else 0),
               "degrid_plan_set_gather")
 
+    def set_host_direct(self, enabled: bool = True) -> None:
+        """Let degrid_host() read pinned host inputs in place (default), or
+        always copy them."""
+        check(load().degrid_plan_set_host_direct(self.handle, 1 if enabled else 0),
+              "degrid_plan_set_host_direct")
+
+    @property
+    def host_direct(self) -> bool:
+        v = ctypes.c_int()
+        check(load().degrid_plan_get_host_direct(self.handle, ctypes.byref(v)),
+              "degrid_plan_get_host_direct")
+        return bool(v.value)
+
     @property
     def gather(self) -> bool:
         v = ctypes.c_int()
@@ -261,13 +274,15 @@ class DegridPlan:
         return out
 
     def degrid_host(self, subgrids, uvw, vis_offsets, scale=None, out=None):
-        """degrid() on HOST data (degrid_execute_host): the call copies the
-        inputs to the device in subgrid groups, overlapping the copies with the
-        sums, and returns when the complex64 [N] host output is complete.
+        """degrid() on HOST data (degrid_execute_host); returns when the
+        complex64 [N] host output is complete.  With pinned (page-locked)
+        subgrids, coordinates and output the kernel reads and writes them in
+        place over the host link; otherwise the call copies the inputs in
+        subgrid groups, overlapping the copies with the sums.
 
         Inputs are CPU torch tensors or numpy arrays (subgrids complex64, or
         for f16/bf16 plans the uint16 code pairs [S, ny, nx, nz, 2] with a
-        float32 scale [S]); pinned (page-locked) tensors give full bandwidth.
+        float32 scale [S]).
         """
         torch = _torch()
 

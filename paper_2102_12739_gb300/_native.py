@@ -50,6 +50,8 @@ SIGNATURES = {
     "degrid_plan_get_direct_runs": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_get_compensated": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_set_gather": (_I, [_P, _I]),
+    "degrid_plan_set_host_direct": (_I, [_P, _I]),
+    "degrid_plan_get_host_direct": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_plan_get_gather": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_measure_fp32_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_measure_l2_read_bw": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),

@@ -254,6 +254,7 @@ static dg_status plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
     p->warps_per_block = dg_max_warps_per_block();
     p->blocks_per_sm = 0;
     p->direct_runs = DG_DIRECT_RUNS_DEFAULT;
+    p->host_direct = 1;
 
     dg_status st = DG_OK;
     const size_t n_uv = g_uv2 ? (size_t)uv_oversample * uv_oversample * uv_support * uv_support
@@ -378,6 +379,22 @@ dg_status degrid_plan_set_gather(degrid_plan_t p, int enabled)
     if (enabled && !dg_gather_supported(p))
         return DG_ERR_UNSUPPORTED;
     p->gather = enabled;
+    return DG_OK;
+}
+
+dg_status degrid_plan_set_host_direct(degrid_plan_t p, int enabled)
+{
+    if (!p || (enabled != 0 && enabled != 1))
+        return DG_ERR_ARG;
+    p->host_direct = enabled;
+    return DG_OK;
+}
+
+dg_status degrid_plan_get_host_direct(degrid_plan_t p, int *enabled)
+{
+    if (!p || !enabled)
+        return DG_ERR_ARG;
+    *enabled = p->host_direct;
     return DG_OK;
 }
 

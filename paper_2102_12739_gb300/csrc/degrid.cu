@@ -374,7 +374,7 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
               const double *__restrict__ uvw, const float *__restrict__ guv,
               const float *__restrict__ gwt, const Schedule sched, float2 *__restrict__ vis_out,
               DeviceStatus *__restrict__ status, const int direct_runs, const bool vec_ok,
-              const float *__restrict__ g2)
+              const float *__restrict__ g2, const bool prefetch_uvw)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // [w table (optional)] [one WarpSmem per warp]
@@ -383,7 +383,11 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     const int lane = threadIdx.x & 31;
     const int p = lane & 7, j = lane >> 3;
 
-    ClaimerT<kBatchVis> claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), nullptr, 0});
+    // coordinates in device memory are prefetched into L2 a chunk ahead;
+    // coordinates read in place from host memory are not (the host link
+    // bounds those calls, and one batch of lead hides its latency)
+    ClaimerT<kBatchVis> claimer(sched, lane,
+                                Prefetch{prefetch_uvw ? uvw : nullptr, 3 * (int)sizeof(double), nullptr, 0});
     Batch bB = claimer.claim();         // rows in flight
     if (bB.n == 0)
         return;
@@ -479,7 +483,7 @@ cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const 
                         p->geo.nz % Storage<DT>::kQuad == 0;
     degrid_kernel<DT, COMP, DIRECT, T2D><<<grid_blocks, threads, smem, st>>>(
         p->geo, subgrids, scale, uvw, p->guv, p->gw, sched, out, p->status, p->direct_runs, vec_ok,
-        p->guv2);
+        p->guv2, !p->host_inputs);
     return cudaGetLastError();
 }
 

@@ -1,14 +1,26 @@
 // degrid_execute_host: the degridding call with inputs and output in host
-// memory.  The subgrid stack is split into groups of consecutive subgrids
-// (about 64 MB of subgrid data each); for every group the plan's three
-// streams run
+// memory, in one of two ways.
+//
+// In place (the default when the subgrids, coordinates and output are
+// page-locked, i.e. mapped into the GPU's address space): the kernel reads
+// the coordinates and the footprint rows it needs straight from host memory
+// over the host link and writes the visibilities back the same way; only the
+// offsets (and unmapped scales) are copied.  A dense list touches a small
+// part of its subgrid (on the 64-line benchmark 1 % of the stack), so the
+// link carries the coordinates and little else.
+//
+// By copies (pageable buffers, a plan with the gather kernel, or in-place
+// access disabled): the subgrid stack is split into groups of consecutive
+// subgrids (about 64 MB of subgrid data each); for every group the plan's
+// three streams run
 //   copy-in:   subgrids, coordinates, rebased offsets (and scales) -> slot
 //   sums:      degrid_execute on the slot                  (waits copy-in)
 //   copy-out:  visibilities slot -> host                   (waits sums)
 // through a ring of two device slots, so the copies of group g + 1 and the
 // copy-out of group g - 1 overlap the sums of group g.  Groups whose lists
-// are empty are skipped without copying their subgrids.  The call returns
-// when the host output is complete.
+// are empty are skipped without copying their subgrids.
+//
+// Either way the call returns when the host output is complete.
 #include <string.h>
 
 #include <algorithm>
@@ -50,6 +62,9 @@ struct dg_host_exec {
     int64_t cap_vis = 0;            // per slot
     int64_t *h_offs = nullptr;      // pinned: rebased offsets of every group
     size_t cap_h_offs = 0;
+    int64_t *d_offs = nullptr;      // in-place calls: the offsets, and scales if unmapped
+    float *d_scale = nullptr;
+    int cap_direct = 0;             // subgrids d_offs / d_scale hold
 };
 
 void dg_free_host_exec(degrid_plan *p)
@@ -70,6 +85,8 @@ void dg_free_host_exec(degrid_plan *p)
         if (x->ev_out[k])
             cudaEventDestroy(x->ev_out[k]);
     }
+    cudaFree(x->d_offs);
+    cudaFree(x->d_scale);
     if (x->s_in)
         cudaStreamDestroy(x->s_in);
     if (x->s_run)
@@ -146,6 +163,60 @@ struct Group {
     size_t h_at;        // position of its rebased offsets in the pinned buffer
 };
 
+// Device address under which the GPU reads host buffer h in place:
+// page-locked memory mapped into the device's address space; else nullptr.
+void *mapped(const void *h)
+{
+    if (!h)
+        return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();             // clear the error of an unknown pointer
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// The in-place form: the kernel reads subgrids, coordinates (and mapped
+// scales) from host memory and writes the output there.
+dg_status execute_in_place(degrid_plan *p, int n_subgrids, const void *sub_d, const float *subgrid_scale,
+                           const float *scale_d, const double *uvw_d, const int64_t *vis_offsets,
+                           int64_t n_vis, float *out_d)
+{
+    dg_host_exec *x = p->hostx;
+    cudaError_t e = cudaSuccess;
+    const bool need_scale = p->dtype != DG_C64 && !scale_d;
+    if (n_subgrids > x->cap_direct) {
+        cudaFree(x->d_offs);
+        cudaFree(x->d_scale);
+        x->d_offs = nullptr;
+        x->d_scale = nullptr;
+        x->cap_direct = 0;
+        e = cudaMalloc(&x->d_offs, sizeof(int64_t) * ((size_t)n_subgrids + 1));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&x->d_scale, sizeof(float) * (size_t)n_subgrids);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+        x->cap_direct = n_subgrids;
+    }
+    e = cudaMemcpyAsync(x->d_offs, vis_offsets, sizeof(int64_t) * ((size_t)n_subgrids + 1),
+                        cudaMemcpyHostToDevice, x->s_run);
+    if (e == cudaSuccess && need_scale)
+        e = cudaMemcpyAsync(x->d_scale, subgrid_scale, sizeof(float) * (size_t)n_subgrids,
+                            cudaMemcpyHostToDevice, x->s_run);
+    if (e != cudaSuccess)
+        return DG_ERR_CUDA;
+    p->host_inputs = 1;
+    const dg_status st = degrid_execute(p, x->s_run, n_subgrids, sub_d,
+                                        p->dtype == DG_C64 ? nullptr : (need_scale ? x->d_scale : scale_d),
+                                        uvw_d, x->d_offs, n_vis, out_d);
+    p->host_inputs = 0;
+    e = cudaStreamSynchronize(x->s_run);
+    if (st != DG_OK)
+        return st;
+    return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" dg_status degrid_execute_host(degrid_plan_t p, int n_subgrids, const void *subgrids,
@@ -167,6 +238,25 @@ extern "C" dg_status degrid_execute_host(degrid_plan_t p, int n_subgrids, const 
     if (n_vis == 0)
         return DG_OK;
 
+    Guard guard(p->device);
+    if (!guard.ok)
+        return DG_ERR_CUDA;
+    if (!p->hostx) {
+        const cudaError_t ce = create_exec(p);
+        if (ce != cudaSuccess) {
+            dg_free_host_exec(p);
+            return ce == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+        }
+    }
+    if (p->host_direct && !p->gather) {
+        void *sub_d = mapped(subgrids), *uvw_d = mapped(uvw), *out_d = mapped(vis_out);
+        if (sub_d && uvw_d && out_d)
+            return execute_in_place(p, n_subgrids, sub_d, subgrid_scale,
+                                    static_cast<const float *>(mapped(subgrid_scale)),
+                                    static_cast<const double *>(uvw_d), vis_offsets, n_vis,
+                                    static_cast<float *>(out_d));
+    }
+
     const size_t sub_bytes = (size_t)p->geo.plane * elem_bytes(p->dtype);
     const int per_group = (int)std::max<size_t>(1, std::min<size_t>(kGroupBytes / sub_bytes, (size_t)n_subgrids));
     std::vector<Group> groups;
@@ -184,15 +274,9 @@ extern "C" dg_status degrid_execute_host(degrid_plan_t p, int n_subgrids, const 
         max_nv = std::max(max_nv, nv);
     }
 
-    Guard guard(p->device);
-    if (!guard.ok)
-        return DG_ERR_CUDA;
     cudaError_t e = cudaSuccess;
-    if (!p->hostx)
-        e = create_exec(p);
     dg_host_exec *x = p->hostx;
-    if (e == cudaSuccess)
-        e = reserve_slots(p, max_n, max_nv);
+    e = reserve_slots(p, max_n, max_nv);
     if (e == cudaSuccess && h_need > x->cap_h_offs) {
         cudaFreeHost(x->h_offs);
         x->h_offs = nullptr;

@@ -214,6 +214,8 @@ struct degrid_plan {
     int compensated;            // compensated (TwoSum) reduction of the lane partials
     int direct_runs;            // non-uniform halves with at least this many runs take the direct sum
     int gather;                 // sum through the gather kernel (gather.cu)
+    int host_direct;            // degrid_execute_host reads page-locked host inputs in place
+    int host_inputs;            // set during such a call: the kernel's inputs are in host memory
     int max_blocks_degrid;      // occupancy results, 0 = not computed yet
     int max_blocks_adjoint;
     struct dg_host_exec *hostx; // streams and staging of degrid_execute_host (host_exec.cu), lazily

@@ -265,6 +265,18 @@ def test_host_memory_entry_point_matches_device_path():
         again = p.degrid_host(sub_np, w.uvw, w.vis_offsets).numpy()     # pageable numpy
         np.testing.assert_array_equal(again.view(np.uint32), ref.view(np.uint32))
         assert p.status() == 1
+        # pinned inputs with pageable output, and in-place access disabled:
+        # both take the copy pipeline
+        h_uvw = torch.from_numpy(w.uvw).pin_memory()
+        mixed = p.degrid_host(h_sub, h_uvw, w.vis_offsets,
+                              out=torch.empty(w.n_vis, dtype=torch.complex64)).numpy()
+        np.testing.assert_array_equal(mixed.view(np.uint32), ref.view(np.uint32))
+        assert p.host_direct
+        p.set_host_direct(False)
+        copied = p.degrid_host(h_sub, h_uvw, w.vis_offsets).numpy()
+        np.testing.assert_array_equal(copied.view(np.uint32), ref.view(np.uint32))
+        p.set_host_direct(True)
+        assert p.status() == 2
         bad = w.vis_offsets.copy()
         bad[3] = bad[2] - 1                                              # decreasing
         with pytest.raises(dg.DegridError):
@@ -274,6 +286,10 @@ def test_host_memory_entry_point_matches_device_path():
         ref16 = p16.degrid(codes, uvw, offs, scale=scale).cpu().numpy()
         got16 = p16.degrid_host(codes.cpu(), w.uvw, w.vis_offsets, scale=scale.cpu()).numpy()
         np.testing.assert_array_equal(got16.view(np.uint32), ref16.view(np.uint32))
+        # in place, with pinned codes and coordinates; pageable then pinned scales
+        for sc in (scale.cpu(), scale.cpu().pin_memory()):
+            got16p = p16.degrid_host(codes.cpu().pin_memory(), h_uvw, w.vis_offsets, scale=sc).numpy()
+            np.testing.assert_array_equal(got16p.view(np.uint32), ref16.view(np.uint32))
 
 
 @pytest.mark.parametrize("dtype", ["c64", "f16", "bf16"])
