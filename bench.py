@@ -290,47 +290,56 @@ def time_steps(torch, plan, call, steps, flush_buf, stream):
 
 def batched_section(torch, dg, synth, dev, flush, steps):
     """512 subgrids with log-uniform counts in [1e3, 1e6] (segments and arcs):
-    autotuned, captured once in a CUDA graph and replayed."""
+    for each storage type autotuned, captured once in a CUDA graph and
+    replayed."""
     w = synth.workload("batched512")
     gen = torch.Generator(device=dev)
     gen.manual_seed(0)
     sub = torch.randn((w.n_subgrids,) + w.shape + (2,), generator=gen, device=dev,
-                      dtype=torch.float32).view(torch.complex64)[..., 0]
+                      dtype=torch.float32).view(torch.complex64)[..., 0].contiguous()
     uvw = torch.from_numpy(w.uvw).to(dev)
     offs = torch.from_numpy(w.vis_offsets).to(dev)
     out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
-    with dg.DegridPlan(device=dev) as plan:
-        tuned = dg.autotune(plan, sub, uvw, offs, use_cache=False)
-        plan.degrid(sub, uvw, offs, out=out)
-        torch.cuda.synchronize()
-        assert plan.status() == 0
-        graph = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream(device=dev)
-        with torch.cuda.stream(cap):
-            with torch.cuda.graph(graph, stream=cap):
-                plan.degrid(sub, uvw, offs, out=out)
-        stream = torch.cuda.current_stream(dev)
-        for _ in range(3):
-            graph.replay()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        for a, b in ev:
-            flush.zero_()
-            a.record(stream)
-            graph.replay()
-            b.record(stream)
-        torch.cuda.synchronize()
-        ms = sorted(a.elapsed_time(b) for a, b in ev)
-    med = ms[len(ms) // 2]
+    res = {}
+    for dt in ("c64", "f16", "bf16"):
+        codes, scale = (sub, None) if dt == "c64" else dg.pack_subgrids(sub, dt)
+        with dg.DegridPlan(dtype=dt, device=dev) as plan:
+            tuned = dg.autotune(plan, codes, uvw, offs, scale=scale, use_cache=False)
+            plan.degrid(codes, uvw, offs, scale=scale, out=out)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            graph = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream(device=dev)
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(graph, stream=cap):
+                    plan.degrid(codes, uvw, offs, scale=scale, out=out)
+            stream = torch.cuda.current_stream(dev)
+            for _ in range(3):
+                graph.replay()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                graph.replay()
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in ev)
+            del graph
+        med = ms[len(ms) // 2]
+        res[dt] = {"value": w.n_vis / (med * 1e-3), "ms_per_step": med, "tuning": tuned["tuning"],
+                   "autotune_candidates": len(tuned["timings"])}
+        if dt != "c64":
+            del codes, scale
     counts = w.counts()
-    return {"workload": "batched512: 512 subgrids 512x512x4 complex64, visibility counts "
+    return {"workload": "batched512: 512 subgrids 512x512x4, visibility counts "
                         "log-uniform in [1e3, 1e6] (%d..%d, %d total), lists of 1-8 segments "
                         "or arcs; subgrid values from a seeded on-device generator"
                         % (counts.min(), counts.max(), w.n_vis),
-            "value": w.n_vis / (med * 1e-3), "unit": UNIT, "ms_per_step": med, "steps": steps,
-            "cuda_graph": True, "tuning": tuned["tuning"],
-            "autotune_candidates": len(tuned["timings"])}
+            "value": res["c64"]["value"], "unit": UNIT, "ms_per_step": res["c64"]["ms_per_step"],
+            "steps": steps, "cuda_graph": True, "tuning": res["c64"]["tuning"],
+            "autotune_candidates": res["c64"]["autotune_candidates"], "by_storage": res}
 
 
 def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
@@ -681,6 +690,9 @@ def run_ours(args, rank, world):
                 stored_np = {int(s_): deq[k] for k, s_ in enumerate(picked)}
             for comp in ((True,) if dt == "c64" else (False, True)):
                 with dg.DegridPlan(dtype=dt, device=dev, compensated=comp) as p2:
+                    # tuned like the headline plan, over the same candidates
+                    dg.autotune(p2, codes, uvw, offs, scale=scale, candidates=HEADLINE_CANDIDATES,
+                                use_cache=False)
                     p2.enable_timing(args.sweep_steps)
                     o2 = torch.empty_like(out)
 
