@@ -39,10 +39,8 @@
 //
 // Requirements (checked by the host): nz = 4, a separable G_uv table, a
 // 16-byte aligned subgrid stack.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "pipeline.cuh"
+#include "tma.cuh"
 
 namespace dg {
 namespace {
@@ -62,9 +60,7 @@ constexpr int kGStages = DG_GATHER_STAGES;
 
 template <int DT>
 struct GatherShape {
-    static constexpr int kRowBytes = kUV * kW * Storage<DT>::kBytes;     // one footprint row: 256 / 128
-    static constexpr int kPitch = kRowBytes + 16;                        // box row in shared memory
-    static constexpr int kBoxX = kPitch / Storage<DT>::kBytes;           // box width, elements: 34 / 36
+    static constexpr int kPitch = FootprintBox<DT>::kPitch;              // box row in shared memory
     static constexpr int kWarps = DT == DG_C64 ? DG_GATHER_WARPS_C64 : DG_GATHER_WARPS_16;
 };
 
@@ -79,51 +75,6 @@ struct alignas(128) GatherSlot {
     int n;                                                      // visibilities in the stage (1..4)
     int s;                                                      // subgrid
 };
-
-// ---- mbarrier and bulk-copy wrappers ---------------------------------------
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-// One arrival that also announces `bytes` of transfers for the current phase.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-
-// Waits for phase `parity` of the mbarrier, polling at most kSpinLimit
-// times; returns false (on every lane) when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity)
-{
-    bool ok = false;
-    for (int i = 0; i < kSpinLimit && !ok; ++i)
-        ok = mbar_try_wait(bar, parity);
-    return __all_sync(kFull, ok);
-}
-
-// TMA tensor copy of the box at (x, y) of the 2D tensor map into shared
-// memory (128-byte aligned), completing as transfer bytes on the mbarrier.
-__device__ __forceinline__ void tensor_copy_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3}], [%4];"
-                 ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
-                 : "memory");
-}
 
 // Issue side of a warp: the batch being copied and the next one.
 struct GatherIssue {
@@ -176,7 +127,7 @@ __device__ __forceinline__ int issue_stage(GatherIssue &is, GatherSlot<DT> &sl, 
         const int nvalid = __popc(__ballot_sync(kFull, copy));
         // the slot's earlier contents were read through the generic proxy;
         // the tensor copies write it through the async proxy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_proxy_async();
         if (lane == 0)
             mbar_arrive_expect_tx(bar, (unsigned)nvalid * (unsigned)sizeof(sl.data[0]));
         __syncwarp();
@@ -328,7 +279,7 @@ degrid_gather_kernel(const Geometry g, const __grid_constant__ CUtensorMap tmap,
 #pragma unroll
         for (int k = 0; k < kGStages; ++k)
             mbar_init(smem_u32(&slots[k].bar), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_mbarrier_init();
     }
     __syncwarp();
     int issued = 0;
@@ -362,32 +313,6 @@ size_t gather_smem(const degrid_plan *p, int warps, size_t slot_bytes)
     return wtable_bytes_host(p->geo) + slot_bytes * kGStages * (size_t)warps;
 }
 
-// The stack as a 2D tensor [S * ny rows][nx * nz elements] with a box of
-// kBoxX x 8 elements: one footprint and its 16-byte pad.
-template <int DT>
-cudaError_t encode_map(const degrid_plan *p, const void *subgrids, int n_subgrids, CUtensorMap *map)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void *fn = nullptr;
-        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                               cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return e != cudaSuccess ? e : cudaErrorNotSupported;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)p->geo.row_stride, (cuuint64_t)n_subgrids * p->geo.ny};
-    const cuuint64_t strides[1] = {(cuuint64_t)p->geo.row_stride * Storage<DT>::kBytes};
-    const cuuint32_t box[2] = {(cuuint32_t)GatherShape<DT>::kBoxX, (cuuint32_t)kUV};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(map, DT == DG_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
-                              2, const_cast<void *>(subgrids), dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int DT, bool COMP>
 cudaError_t launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids, int n_subgrids,
                           const float *scale, const double *uvw, float2 *out, const Schedule &sched,
@@ -405,7 +330,7 @@ cudaError_t launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids,
             smem_set[p->device] = smem;
     }
     CUtensorMap map;
-    cudaError_t e = encode_map<DT>(p, subgrids, n_subgrids, &map);
+    cudaError_t e = encode_footprint_map<DT>(p, subgrids, n_subgrids, &map);
     if (e != cudaSuccess)
         return e;
     degrid_gather_kernel<DT, COMP><<<grid_blocks, kWarps * kWarp, smem, st>>>(
