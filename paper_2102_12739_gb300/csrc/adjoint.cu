@@ -133,6 +133,7 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
     const int lane = threadIdx.x & 31;
     const int p = lane & 7, j = lane >> 3;
 
+    pdl_wait();                         // the chunk table (and the zeroed output) are complete
     Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), vis_in, (int)sizeof(float2)});
     Batch bB = claimer.claim();
     if (bB.n == 0)
@@ -258,10 +259,9 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
         if (p->device < kMaxDevices)
             *set = smem;
     }
-    kernel<<<grid_blocks, p->warps_per_block * kWarp, smem, st>>>(
-        p->geo, uvw, reinterpret_cast<const float2 *>(vis_in), p->guv, p->gw, sched,
-        reinterpret_cast<float2 *>(sub_out), p->status, p->guv2);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(grid_blocks), dim3(p->warps_per_block * kWarp), smem, st, p->geo, uvw,
+                      reinterpret_cast<const float2 *>(vis_in), (const float *)p->guv, (const float *)p->gw,
+                      sched, reinterpret_cast<float2 *>(sub_out), p->status, (const float *)p->guv2);
 }
 
 int dg_max_blocks_per_sm_adjoint(degrid_plan *p)

@@ -386,6 +386,7 @@ degrid_kernel(const Geometry g, const void *__restrict__ subgrids, const float *
     // coordinates in device memory are prefetched into L2 a chunk ahead;
     // coordinates read in place from host memory are not (the host link
     // bounds those calls, and one batch of lead hides its latency)
+    pdl_wait();                         // the chunk table is complete
     ClaimerT<kBatchVis> claimer(sched, lane,
                                 Prefetch{prefetch_uvw ? uvw : nullptr, 3 * (int)sizeof(double), nullptr, 0});
     Batch bB = claimer.claim();         // rows in flight
@@ -481,10 +482,9 @@ cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const 
     // elements per 16 bytes
     const bool vec_ok = (reinterpret_cast<uintptr_t>(subgrids) & 15) == 0 &&
                         p->geo.nz % Storage<DT>::kQuad == 0;
-    degrid_kernel<DT, COMP, DIRECT, T2D><<<grid_blocks, threads, smem, st>>>(
-        p->geo, subgrids, scale, uvw, p->guv, p->gw, sched, out, p->status, p->direct_runs, vec_ok,
-        p->guv2, !p->host_inputs);
-    return cudaGetLastError();
+    return launch_pdl(degrid_kernel<DT, COMP, DIRECT, T2D>, dim3(grid_blocks), dim3(threads), smem, st,
+                      p->geo, subgrids, scale, uvw, (const float *)p->guv, (const float *)p->gw, sched, out,
+                      p->status, p->direct_runs, vec_ok, (const float *)p->guv2, !p->host_inputs);
 }
 
 template <int DT, bool COMP, bool DIRECT, bool T2D>

@@ -262,6 +262,7 @@ degrid_gather_kernel(const Geometry g, const __grid_constant__ CUtensorMap tmap,
     const float4 *wtab = load_wtable(g, gwt, smem_raw);
     const int lane = threadIdx.x & 31;
 
+    pdl_wait();                         // the chunk table is complete
     ClaimerT<kBatch> cl(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), nullptr, 0});
     GatherIssue is;
     is.q = 0;
@@ -333,9 +334,9 @@ cudaError_t launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids,
     cudaError_t e = encode_footprint_map<DT>(p, subgrids, n_subgrids, &map);
     if (e != cudaSuccess)
         return e;
-    degrid_gather_kernel<DT, COMP><<<grid_blocks, kWarps * kWarp, smem, st>>>(
-        p->geo, map, scale, uvw, p->guv, p->gw, sched, out, p->status);
-    return cudaGetLastError();
+    return launch_pdl(degrid_gather_kernel<DT, COMP>, dim3(grid_blocks), dim3(kWarps * kWarp), smem, st,
+                      p->geo, map, scale, uvw, (const float *)p->guv, (const float *)p->gw, sched, out,
+                      p->status);
 }
 
 template <int DT>

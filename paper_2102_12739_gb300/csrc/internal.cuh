@@ -189,6 +189,38 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
 // exceeds it records kFlagTimeout and the warp stops working.
 constexpr int kSpinLimit = 1 << 22;
 
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of one call run back to back on
+// a stream (scan -> chunk table -> sums); each later one is launched with
+// programmatic stream serialisation, so it is scheduled while its
+// predecessor still runs and does its independent setup (w table, barriers)
+// meanwhile.  pdl_wait() returns once the predecessor grid has completed and
+// its writes are visible: every kernel calls it before it reads or writes
+// anything its predecessor (or the work before that) touches.
+// pdl_trigger() lets the successor be scheduled early.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches `kernel` so that it may overlap the tail of the previous kernel
+// in the stream (it must call pdl_wait() before touching shared data).
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 }  // namespace dg
 
 // The plan object behind degrid_plan_t.

@@ -34,6 +34,7 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
     __shared__ long long warp_sums[kScanThreads / kWarp];
     __shared__ long long carry_sh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    pdl_trigger();                          // the chunk table (or sums) kernel may be scheduled now
     if (tid == 0) {
         carry_sh = 0;
         *work_counter = 0;
@@ -108,6 +109,8 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
 __global__ void chunk_fill(const int *__restrict__ prefix, const int64_t *__restrict__ offs,
                            int S, int chunk, ChunkDesc *__restrict__ chunks)
 {
+    pdl_trigger();
+    pdl_wait();                             // prefix[] complete
     for (int s = blockIdx.x; s < S; s += gridDim.x) {
         const int lo = prefix[s], hi = prefix[s + 1];
         const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
@@ -134,8 +137,8 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
     if (err != cudaSuccess || n_subgrids == 0 || small)
         return err;
     const int blocks = n_subgrids < 4096 ? n_subgrids : 4096;
-    chunk_fill<<<blocks, 256, 0, st>>>(prefix, vis_offsets, n_subgrids, chunk, chunks);
-    return cudaGetLastError();
+    return launch_pdl(chunk_fill, dim3(blocks), dim3(256), 0, st, (const int *)prefix, vis_offsets,
+                      n_subgrids, chunk, chunks);
 }
 
 }  // namespace dg
