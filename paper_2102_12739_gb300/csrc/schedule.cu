@@ -7,38 +7,37 @@
 // subgrids are numbered consecutively, and a persistent grid claims them
 // with an atomic counter, so the load is balanced whatever the counts are.
 //
-// Two small kernels build the chunk table on the device, so no host
-// synchronisation is needed and the whole call can be captured in a CUDA
-// graph:
-//   1. chunk_prefix: one block validates vis_offsets and scans
-//      ceil(count_s / chunk) into prefix[S + 1];
-//   2. chunk_fill: writes (s, count, first visibility) for every chunk.
-// For small calls (few subgrids and chunks, bounded on the host) the block of
-// chunk_prefix also writes the chunks, saving a launch.
+// The chunk table is built on the device, so no host synchronisation is
+// needed and the whole call can be captured in a CUDA graph.  For up to
+// kSchedMaxS subgrids one kernel does it: every block scans
+// ceil(count_s / chunk) over all subgrids into its shared memory (the scan
+// is small and every block gets the same result), block 0 also validates
+// vis_offsets and resets the work counter, and each block writes the chunk
+// descriptors (s, count, first visibility) of its share of the subgrids.
+// Larger stacks take two kernels: chunk_prefix (one block scans into
+// prefix[S + 1] in global memory) and chunk_fill (the descriptors).
 #include "internal.cuh"
 
 namespace dg {
 namespace {
 
 constexpr int kScanThreads = 1024;
+constexpr int kSchedMaxS = 4096;            // subgrids the one-kernel schedule scans in shared memory
+constexpr int kSchedMaxBlocks = 1024;
 
-constexpr int kSmallSubgrids = 32;          // one-launch schedule: at most this many subgrids
-constexpr int kSmallChunks = 8192;          // and at most this many chunks (host bound)
-
-__global__ void __launch_bounds__(kScanThreads)
-chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
-             int *__restrict__ prefix, int *__restrict__ n_chunks, int capacity,
-             int *__restrict__ work_counter, DeviceStatus *__restrict__ status,
-             ChunkDesc *__restrict__ fill_chunks)
+// Exclusive scan of ceil(count_s / chunk) over s < S into pre[0..S] (shared
+// or global memory), each entry clamped to `capacity`; every thread of the
+// block gets the (clamped) total.  With `lead` the block records malformed
+// offsets and an overflowing total in the status flags.
+__device__ long long scan_chunks(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
+                                 int *pre, int capacity, bool lead, DeviceStatus *status)
 {
     __shared__ long long warp_sums[kScanThreads / kWarp];
     __shared__ long long carry_sh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    pdl_trigger();                          // the chunk table (or sums) kernel may be scheduled now
     if (tid == 0) {
         carry_sh = 0;
-        *work_counter = 0;
-        if (S >= 0 && (offs[0] != 0 || offs[S] != n_vis))
+        if (lead && (offs[0] != 0 || offs[S] != n_vis))
             atomicOr(&status->flags, kFlagOffsets);
     }
     __syncthreads();
@@ -48,10 +47,12 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
         if (s < S) {
             const int64_t lo = offs[s], hi = offs[s + 1];
             const bool ok = lo >= 0 && lo <= hi && hi <= n_vis;
-            if (!ok)
-                atomicOr(&status->flags, kFlagOffsets);
-            else
+            if (!ok) {
+                if (lead)
+                    atomicOr(&status->flags, kFlagOffsets);
+            } else {
                 cnt = (hi - lo + chunk - 1) / chunk;
+            }
         }
         // inclusive scan: within warps, then over warp totals
         long long x = cnt;
@@ -77,32 +78,65 @@ chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
         __syncthreads();
         const long long before = carry_sh + (wid ? warp_sums[wid - 1] : 0) + x - cnt;
         if (s < S)
-            prefix[s] = (int)min(before, (long long)capacity);
+            pre[s] = (int)min(before, (long long)capacity);
         __syncthreads();
         if (tid == 0)
             carry_sh += warp_sums[kScanThreads / kWarp - 1];
         __syncthreads();
     }
-    if (tid == 0) {
-        long long total = carry_sh;
-        if (total > capacity) {
+    long long total = carry_sh;
+    if (total > capacity) {
+        if (lead && tid == 0)
             atomicOr(&status->flags, kFlagCapacity);
-            total = capacity;
+        total = capacity;
+    }
+    if (tid == 0)
+        pre[S] = (int)total;
+    __syncthreads();
+    return total;
+}
+
+// Descriptors of the chunks of subgrids s = first, first + step, ...
+__device__ __forceinline__ void fill_chunks(const int *pre, const int64_t *__restrict__ offs, int S, int chunk,
+                                            ChunkDesc *__restrict__ chunks, int first, int step)
+{
+    for (int s = first; s < S; s += step) {
+        const int lo = pre[s], hi = pre[s + 1];
+        const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
+        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+            const int64_t first_vis = vis_lo + (int64_t)(k - lo) * chunk;
+            const int64_t last = min(first_vis + (int64_t)chunk, vis_hi);
+            chunks[k] = ChunkDesc{s, (int)(last - first_vis), (long long)first_vis};
         }
-        prefix[S > 0 ? S : 0] = (int)total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+chunk_schedule(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk, int *__restrict__ n_chunks,
+               int capacity, int *__restrict__ work_counter, DeviceStatus *__restrict__ status,
+               ChunkDesc *__restrict__ chunks)
+{
+    __shared__ int pre[kSchedMaxS + 1];
+    pdl_trigger();                          // the summing kernel may be scheduled now
+    const bool lead = blockIdx.x == 0;
+    const long long total = scan_chunks(offs, S, n_vis, chunk, pre, capacity, lead, status);
+    if (lead && threadIdx.x == 0) {
+        *work_counter = 0;
         *n_chunks = (int)total;
     }
-    if (!fill_chunks)
-        return;
-    __syncthreads();                        // prefix[] visible to the whole block
-    for (int s = 0; s < S; ++s) {
-        const int lo = prefix[s], hi = prefix[s + 1];
-        const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
-        for (int k = lo + tid; k < hi; k += kScanThreads) {
-            const int64_t first = vis_lo + (int64_t)(k - lo) * chunk;
-            const int64_t last = min(first + (int64_t)chunk, vis_hi);
-            fill_chunks[k] = ChunkDesc{s, (int)(last - first), (long long)first};
-        }
+    fill_chunks(pre, offs, S, chunk, chunks, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+chunk_prefix(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk,
+             int *__restrict__ prefix, int *__restrict__ n_chunks, int capacity,
+             int *__restrict__ work_counter, DeviceStatus *__restrict__ status)
+{
+    pdl_trigger();                          // the chunk table kernel may be scheduled now
+    const long long total = scan_chunks(offs, S, n_vis, chunk, prefix, capacity, true, status);
+    if (threadIdx.x == 0) {
+        *work_counter = 0;
+        *n_chunks = (int)total;
     }
 }
 
@@ -111,15 +145,7 @@ __global__ void chunk_fill(const int *__restrict__ prefix, const int64_t *__rest
 {
     pdl_trigger();
     pdl_wait();                             // prefix[] complete
-    for (int s = blockIdx.x; s < S; s += gridDim.x) {
-        const int lo = prefix[s], hi = prefix[s + 1];
-        const int64_t vis_lo = offs[s], vis_hi = offs[s + 1];
-        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-            const int64_t first = vis_lo + (int64_t)(k - lo) * chunk;
-            const int64_t last = min(first + (int64_t)chunk, vis_hi);
-            chunks[k] = ChunkDesc{s, (int)(last - first), (long long)first};
-        }
-    }
+    fill_chunks(prefix, offs, S, chunk, chunks, blockIdx.x, gridDim.x);
 }
 
 }  // namespace
@@ -129,12 +155,16 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
                             ChunkDesc *chunks, int capacity, int *work_counter,
                             DeviceStatus *status)
 {
-    const bool small = n_subgrids <= kSmallSubgrids && n_vis / chunk + n_subgrids <= kSmallChunks;
-    chunk_prefix<<<1, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, prefix,
-                                             n_chunks, capacity, work_counter, status,
-                                             small ? chunks : nullptr);
+    if (n_subgrids <= kSchedMaxS) {
+        const int blocks = n_subgrids < 1 ? 1 : (n_subgrids < kSchedMaxBlocks ? n_subgrids : kSchedMaxBlocks);
+        chunk_schedule<<<blocks, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, n_chunks,
+                                                        capacity, work_counter, status, chunks);
+        return cudaGetLastError();
+    }
+    chunk_prefix<<<1, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, prefix, n_chunks,
+                                             capacity, work_counter, status);
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || n_subgrids == 0 || small)
+    if (err != cudaSuccess)
         return err;
     const int blocks = n_subgrids < 4096 ? n_subgrids : 4096;
     return launch_pdl(chunk_fill, dim3(blocks), dim3(256), 0, st, (const int *)prefix, vis_offsets,

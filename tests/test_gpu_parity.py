@@ -652,3 +652,25 @@ def test_diff32_gradient_matches_central_differences():
             worst = max(worst, abs(fd - g) / scale)
         assert p.status() == 0
     assert worst <= 1e-3, worst
+
+
+def test_many_subgrids_take_the_two_kernel_schedule():
+    # more than 4096 subgrids: the scan and the chunk table are two kernels
+    # (one block scans all counts) instead of one; small 16 x 16 x 4 subgrids,
+    # ragged and empty lists, element by element against the oracle
+    d = dev()
+    shape = (16, 16, 4)
+    rng = np.random.default_rng(71)
+    counts = rng.integers(0, 24, 5000)
+    counts[[0, 17, 4999]] = 0
+    w = small_workload(list(counts), kind="scatter", shape=shape, seed=71)
+    sub_np = synth.subgrid_stack(len(counts), shape=shape)
+    sub, uvw, offs = upload(w, sub_np)
+    with dg.DegridPlan(shape=shape, device=d) as p:
+        for chunk in (32, 64):
+            p.set_tuning(chunk, 8, 0)
+            got = p.degrid(sub, uvw, offs).cpu().numpy()
+            assert p.status() == 0
+            ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+            assert bad == 0
+            assert rel_l2(got, ref) <= TOL["c64"]
