@@ -674,3 +674,42 @@ def test_many_subgrids_take_the_two_kernel_schedule():
             ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
             assert bad == 0
             assert rel_l2(got, ref) <= TOL["c64"]
+
+
+@pytest.mark.parametrize("nz", [5, 8])
+@pytest.mark.parametrize("dtype", ["c64", "f16", "bf16"])
+def test_deep_w_axis_with_unaligned_footprints(nz, dtype):
+    # nz > 4: a footprint starts at any z0 in [0, nz - 4], so its four w
+    # samples are often not 16-byte aligned (the element-wise loads); planes
+    # are not square.  A line whose w sweeps the whole axis (runs, and a
+    # change of z0 inside runs of x, y) and scattered points; the direct arm
+    # must give the cached path's bits, the adjoint the oracle's values.
+    d = dev()
+    shape = (40, 56, nz)
+    ny, nx, _ = shape
+    w = small_workload([1500, 0, 1200], kind="line", shape=shape, seed=80 + nz)
+    rng = np.random.default_rng(90 + nz)
+    w_hi = nz - 3 - 1e-3
+    w.uvw[:1500, 2] = np.linspace(1.0, w_hi, 1500)
+    w.uvw[1500:, 0] = rng.uniform(*synth.uv_box(nx), 1200)
+    w.uvw[1500:, 1] = rng.uniform(*synth.uv_box(ny), 1200)
+    w.uvw[1500:, 2] = rng.uniform(1.0, w_hi, 1200)
+    c, bad = oracle.coords(w.uvw, shape)
+    assert bad == 0 and len(np.unique(c[:, 2])) == nz - 3
+    sub_np = synth.subgrid_stack(3, shape=shape)
+    sub, uvw, offs = upload(w, sub_np)
+    codes, scale = (sub, None) if dtype == "c64" else dg.pack_subgrids(sub, dtype)
+    ref, _ = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    with dg.DegridPlan(shape=shape, dtype=dtype, device=d) as p:
+        got = p.degrid(codes, uvw, offs, scale=scale).cpu().numpy()
+        p.set_direct_runs(1)
+        direct = p.degrid(codes, uvw, offs, scale=scale).cpu().numpy()
+        assert p.status() == 0
+    assert rel_l2(got, ref) <= TOL[dtype]
+    np.testing.assert_array_equal(direct.view(np.uint32), got.view(np.uint32))
+    if dtype == "c64":
+        y = synth.adjoint_vis(w.n_vis)
+        with dg.DegridPlan(shape=shape, device=d) as p:
+            g = p.grid(torch.from_numpy(y).to(d), uvw, offs, 3).cpu().numpy()
+        gref, _ = oracle.grid(G_UV, G_W, shape, 3, w.uvw, w.vis_offsets, y)
+        assert rel_l2(g, gref) <= TOL["c64"]
