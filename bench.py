@@ -381,10 +381,28 @@ def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
                            "direct" if tuned["tuning"]["direct_runs"] < 33 else "footprint cache"),
                    "tuning": tuned["tuning"]}
         del codes, scale
+    # gridding (the adjoint) of the same coverage: the run-accumulating kernel
+    # (float2 atomics at every run end) and the tensor reduce-add kernel
+    y = torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(dev)
+    grid_out = torch.empty((w.n_subgrids,) + w.shape, dtype=torch.complex64, device=dev)
+    gridding = {}
+    for gather in (False, True):
+        with dg.DegridPlan(device=dev, gather=gather) as plan:
+            plan.enable_timing(steps)
+            for _ in range(3):
+                plan.grid(y, uvw, offs, w.n_subgrids, out=grid_out)
+            for _ in range(steps):
+                flush.zero_()
+                plan.grid(y, uvw, offs, w.n_subgrids, out=grid_out)
+            k_ms = sorted(plan.kernel_times_ms(steps))
+            assert plan.status() == 0
+        kms = k_ms[len(k_ms) // 2]
+        gridding["tensor reduce-add" if gather else "run accumulation + atomics"] = {
+            "kernel_ms": kms, "value": w.n_vis / (kms * 1e-3), "unit": "gridded visibilities/s"}
     return {"workload": "scatter16_250k: 16 subgrids 512x512x4, 250,000 visibilities each "
                         "scattered uniformly over the valid box (no footprint shared by "
                         "consecutive visibilities)", "unit": UNIT, "steps": steps,
-            "l2_read_gbs_measured": l2_gbs, "by_storage": res}
+            "l2_read_gbs_measured": l2_gbs, "by_storage": res, "gridding": gridding}
 
 
 def latency_section(torch, dg, synth, dev, steps):

@@ -187,10 +187,15 @@ dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
  * Same arithmetic in the same order as the footprint-cache path: results
  * are bitwise identical; the compensated setting applies.  Only the speed
  * differs: it wins when footprints are scattered and loses on dense lists,
- * where one cached M serves hundreds of visibilities.  Needs nz = 4 and a
- * separable G_uv table: enabling it on another plan returns
- * DG_ERR_UNSUPPORTED.  Returns DG_OK, DG_ERR_ARG (enabled not 0 / 1) or
- * DG_ERR_UNSUPPORTED.
+ * where one cached M serves hundreds of visibilities.  The setting also
+ * switches grid_adjoint_execute (output stack 16-byte aligned) to its
+ * counterpart for scattered coverage: each visibility's 8 x 8 x 4
+ * contribution is written to shared memory and added to the stack by one
+ * tensor reduce-add of the copy engine, instead of the run accumulation
+ * with float2 atomics (FP32 additions in another order: the last bits
+ * differ).  Needs nz = 4 and a separable G_uv table: enabling it on another
+ * plan returns DG_ERR_UNSUPPORTED.  Returns DG_OK, DG_ERR_ARG (enabled not
+ * 0 / 1) or DG_ERR_UNSUPPORTED.
  */
 dg_status degrid_plan_set_gather(degrid_plan_t plan, int enabled);
 dg_status degrid_plan_get_gather(degrid_plan_t plan, int *enabled);

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(OUT_DIR, "libdegrid.so")
 
 SOURCES = ["api.cu", "schedule.cu", "degrid.cu", "adjoint.cu", "aux_kernels.cu", "noalloc.cu",
            "host_exec.cu", "peak.cu",
-           "gather.cu"]
+           "gather.cu", "scatter.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "-I", INCLUDE, "-I", CSRC]

@@ -567,6 +567,14 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
+    if (p->gather && aligned(sub_out, 16)) {
+        // scattered coverage: every visibility's tile added by a tensor reduce, one CTA per SM
+        const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, 1, dg_scatter_warps());
+        KernelTimer timer(p, s);
+        e = dg_launch_scatter(p, s, n_subgrids, uvw, vis_in, sub_out, blocks);
+        timer.stop();
+        return from_cuda(e);
+    }
     if (p->max_blocks_adjoint == 0)
         p->max_blocks_adjoint = dg_max_blocks_per_sm_adjoint(p);
     const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, p->max_blocks_adjoint, p->warps_per_block);

@@ -270,6 +270,9 @@ cudaError_t dg_launch_coords(degrid_plan *p, cudaStream_t st, const double *uvw,
 cudaError_t dg_launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids, int n_subgrids,
                              const float *scale, const double *uvw, float *vis_out, int grid_blocks);
 int dg_gather_warps(dg_dtype dtype);            // warps per CTA of the gather kernel
+cudaError_t dg_launch_scatter(degrid_plan *p, cudaStream_t st, int n_subgrids, const double *uvw,
+                              const float *vis_in, float *sub_out, int grid_blocks);
+int dg_scatter_warps();                         // warps per CTA of the scattered gridding kernel
 bool dg_gather_supported(const degrid_plan *p);
 int dg_max_blocks_per_sm_degrid(degrid_plan *p);
 int dg_max_warps_per_block();        // largest warps_per_block the kernels are built for

@@ -82,12 +82,10 @@ __device__ __forceinline__ void fence_mbarrier_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// The tensor map of a stack of n_subgrids subgrids (host side), with boxes
-// of 8 rows x box_x elements (FootprintBox<DT>::kBoxX for padded rows, or
-// 32 for the bare footprint).
-template <int DT>
-cudaError_t encode_footprint_map(const degrid_plan *p, const void *subgrids, int n_subgrids, CUtensorMap *map,
-                                 int box_x = FootprintBox<DT>::kBoxX)
+// A 2D tensor map (host side): dim0 x dim1 elements of type `type`, rows
+// `stride` bytes apart, boxes of box0 x box1 elements, no swizzle.
+inline cudaError_t encode_2d(CUtensorMap *map, void *base, CUtensorMapDataType type, uint64_t dim0,
+                             uint64_t dim1, uint64_t stride, uint32_t box0, uint32_t box1)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -99,15 +97,27 @@ cudaError_t encode_footprint_map(const degrid_plan *p, const void *subgrids, int
             return e != cudaSuccess ? e : cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const cuuint64_t dims[2] = {(cuuint64_t)p->geo.row_stride, (cuuint64_t)n_subgrids * p->geo.ny};
-    const cuuint64_t strides[1] = {(cuuint64_t)p->geo.row_stride * Storage<DT>::kBytes};
-    const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)kUV};
+    const cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
+    const cuuint64_t strides[1] = {(cuuint64_t)stride};
+    const cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(map, DT == DG_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
-                              2, const_cast<void *>(subgrids), dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = encode(map, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// The tensor map of a stack of n_subgrids subgrids (host side), with boxes
+// of 8 rows x box_x elements (FootprintBox<DT>::kBoxX for padded rows, or
+// 32 for the bare footprint).
+template <int DT>
+cudaError_t encode_footprint_map(const degrid_plan *p, const void *subgrids, int n_subgrids, CUtensorMap *map,
+                                 int box_x = FootprintBox<DT>::kBoxX)
+{
+    return encode_2d(map, const_cast<void *>(subgrids),
+                     DT == DG_C64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32,
+                     (uint64_t)p->geo.row_stride, (uint64_t)n_subgrids * p->geo.ny,
+                     (uint64_t)p->geo.row_stride * Storage<DT>::kBytes, (uint32_t)box_x, (uint32_t)kUV);
 }
 
 }  // namespace
