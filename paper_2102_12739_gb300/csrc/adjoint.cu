@@ -4,9 +4,10 @@
 // (or G[fv][fu][b][a] g_w[c] * vis[i] with a non-separable 2D G_uv table).
 // The weights are real, so this is the exact transpose of degrid.cu.
 //
-// The batch pipeline is the forward kernel's (pipeline.cuh): lane i of a
-// batch snaps visibility i, copies its g_u / g_v rows into the warp's stage
-// and loads its value y_i one batch ahead.  The scatter is factored like the
+// The pipeline is the forward kernel's (pipeline.cuh): steps of 64
+// visibilities in two halves of 32; lane i of a half snaps visibility i,
+// copies its g_u / g_v rows into the warp's stage and loads its value y_i a
+// step ahead.  The scatter is factored like the
 // forward sum: for a run of visibilities that share the footprint start and
 // the w-kernel row,
 //   sub[y0+b][x0+a][z0+c] += g_w[c] T[b][a],   T[b][a] = sum_i g_v,i[b] g_u,i[a] y_i,
@@ -18,7 +19,7 @@
 // transpose with XOR-swizzled 16-byte slots, free of bank conflicts) and lane
 // 8j + p adds column a = p of rows 2j, 2j+1 to the subgrid with 8 float2
 // atomics (c = 0..3).  Dense lists have runs of hundreds of visibilities, so
-// the atomics are a small fraction of the work.  Batches whose 32
+// the atomics are a small fraction of the work.  Halves whose 32
 // visibilities share one run take a branch-free path.
 #include "pipeline.cuh"
 
@@ -31,8 +32,10 @@ namespace {
 
 constexpr int kMaxWarps = 8;
 
+constexpr int kStepVis = 2 * kBatch;        // visibilities per pipeline step (two halves)
+
 struct alignas(128) WarpSmem {
-    RowStage st[2];
+    RowStage st[2][2];          // [stage][half]
     float4 t[8][4][8];          // flush transpose: [p][j][slot a ^ p] = (T[2j][a], T[2j+1][a])
 };
 
@@ -120,6 +123,71 @@ __device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *_
     atomicAdd(e1 + 3, make_float2(sum.z * gw.w, sum.w * gw.w));
 }
 
+// The run state of a warp: T accumulates the run (key, fw) of subgrid s.
+struct RunState {
+    float2 T[2][8];
+    int key, fw, s;             // key -1: no run
+    float2 *sub_s;
+};
+
+// Accumulates one half batch (32 visibilities, stage S, issued info I,
+// values y: lane i holds visibility i's) into the warp's runs.
+template <bool T2D>
+__device__ __forceinline__ void accumulate_half(RunState &rs, WarpSmem &ws, const RowStage &S, const Issued &I,
+                                                float2 yv, const Geometry &g, const float4 *wtab,
+                                                const float *__restrict__ gwt, const float *__restrict__ g2,
+                                                int p, int j)
+{
+    if (I.uniform) {
+        if (I.key0 != rs.key || I.fw0 != rs.fw) {
+            if (rs.key >= 0)
+                flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+            rs.key = I.key0;
+            rs.fw = I.fw0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * k + p;
+            float2 y;
+            y.x = __shfl_sync(kFull, yv.x, r);
+            y.y = __shfl_sync(kFull, yv.y, r);
+            accumulate_vis<T2D>(rs.T, S, g2, r, T2D ? __shfl_sync(kFull, I.blk, r) : 0, j, y);
+        }
+    } else {
+        // visibilities in list order; each change of (footprint, w row)
+        // ends the run; invalid visibilities (key -1) add nothing
+#pragma unroll 1
+        for (int k = 0; k < 4; ++k) {
+            const int r = 8 * k + p;
+            const int kr = __shfl_sync(kFull, I.key, r);
+            const int fr = __shfl_sync(kFull, I.fw, r);
+            const int br = T2D ? __shfl_sync(kFull, I.blk, r) : 0;
+            float2 y;
+            y.x = __shfl_sync(kFull, yv.x, r);
+            y.y = __shfl_sync(kFull, yv.y, r);
+            bool done = kr < 0;
+#pragma unroll 1
+            while (true) {
+                const unsigned todo = __ballot_sync(kFull, !done);
+                if (todo == 0)
+                    break;
+                const int leader = __ffs(todo) - 1;
+                const int lk = __shfl_sync(kFull, kr, leader);
+                const int lf = __shfl_sync(kFull, fr, leader);
+                if (lk != rs.key || lf != rs.fw) {
+                    if (rs.key >= 0)
+                        flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+                    rs.key = lk;
+                    rs.fw = lf;
+                }
+                const bool mine = !done && kr == lk && fr == lf;
+                accumulate_vis<T2D>(rs.T, S, g2, r, br, j, mine ? y : make_float2(0.f, 0.f));
+                done = done || mine;
+            }
+        }
+    }
+}
+
 template <bool T2D>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_ADJOINT_MIN_BLOCKS)
 adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *__restrict__ vis_in,
@@ -134,102 +202,67 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
     const int p = lane & 7, j = lane >> 3;
 
     pdl_wait();                         // the chunk table (and the zeroed output) are complete
-    Claimer claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), vis_in, (int)sizeof(float2)});
+    ClaimerT<kStepVis> claimer(sched, lane, Prefetch{uvw, 3 * (int)sizeof(double), vis_in, (int)sizeof(float2)});
     Batch bB = claimer.claim();
     if (bB.n == 0)
         return;
-    Issued iB = issue_rows<RowStage, !T2D>(bB, load_uvw(uvw, bB, lane), g, ws.st[0], guv, lane, status);
-    float2 yB = load_y(vis_in, bB, lane);
+    Issued iB0 = issue_rows<RowStage, !T2D>(half_of(bB, 0), load_uvw(uvw, half_of(bB, 0), lane), g,
+                                            ws.st[0][0], guv, lane, status, false);
+    Issued iB1 = issue_rows<RowStage, !T2D>(half_of(bB, 1), load_uvw(uvw, half_of(bB, 1), lane), g,
+                                            ws.st[0][1], guv, lane, status, true);
+    float2 yB0 = load_y(vis_in, half_of(bB, 0), lane), yB1 = load_y(vis_in, half_of(bB, 1), lane);
     Batch bC = claimer.advance(bB);
-    Coords3 cC = load_uvw(uvw, bC, lane);
+    Coords3 cC0 = load_uvw(uvw, half_of(bC, 0), lane);
+    Coords3 cC1 = load_uvw(uvw, half_of(bC, 1), lane);
 
     int stage = 0;
-    float2 T[2][8];
+    RunState rs;
 #pragma unroll
     for (int a = 0; a < 8; ++a)
-        T[0][a] = T[1][a] = make_float2(0.f, 0.f);
-    int run_key = -1, run_fw = 0, run_s = -1;   // run being accumulated in T (key -1: none)
-    float2 *sub_s = sub_out;
+        rs.T[0][a] = rs.T[1][a] = make_float2(0.f, 0.f);
+    rs.key = -1;
+    rs.fw = 0;
+    rs.s = -1;
+    rs.sub_s = sub_out;
 
     while (bB.n > 0) {
         const Batch bA = bB;
-        const Issued iA = iB;
-        const float2 yA = yB;
+        const Issued iA0 = iB0, iA1 = iB1;
+        const float2 yA0 = yB0, yA1 = yB1;
         const int sA = stage;
         bB = bC;
         if (bB.n > 0) {
-            iB = issue_rows<RowStage, !T2D>(bB, cC, g, ws.st[sA ^ 1], guv, lane, status);
-            yB = load_y(vis_in, bB, lane);
+            iB0 = issue_rows<RowStage, !T2D>(half_of(bB, 0), cC0, g, ws.st[sA ^ 1][0], guv, lane, status,
+                                             false);
+            iB1 = issue_rows<RowStage, !T2D>(half_of(bB, 1), cC1, g, ws.st[sA ^ 1][1], guv, lane, status,
+                                             true);
+            yB0 = load_y(vis_in, half_of(bB, 0), lane);
+            yB1 = load_y(vis_in, half_of(bB, 1), lane);
         }
         bC = claimer.advance(bC);
-        cC = load_uvw(uvw, bC, lane);
+        cC0 = load_uvw(uvw, half_of(bC, 0), lane);
+        cC1 = load_uvw(uvw, half_of(bC, 1), lane);
         if (bB.n > 0)
             cp_async_wait<1>();
         else
             cp_async_wait<0>();
         __syncwarp();
 
-        const RowStage &S = ws.st[sA];
-        if (bA.s != run_s) {
-            if (run_key >= 0)
-                flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
-            run_key = -1;
-            run_s = bA.s;
-            sub_s = sub_out + (int64_t)bA.s * g.plane;
+        if (bA.s != rs.s) {
+            if (rs.key >= 0)
+                flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+            rs.key = -1;
+            rs.s = bA.s;
+            rs.sub_s = sub_out + (int64_t)bA.s * g.plane;
         }
-        if (iA.uniform) {
-            if (iA.key0 != run_key || iA.fw0 != run_fw) {
-                if (run_key >= 0)
-                    flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
-                run_key = iA.key0;
-                run_fw = iA.fw0;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int r = 8 * k + p;
-                float2 y;
-                y.x = __shfl_sync(kFull, yA.x, r);
-                y.y = __shfl_sync(kFull, yA.y, r);
-                accumulate_vis<T2D>(T, S, g2, r, T2D ? __shfl_sync(kFull, iA.blk, r) : 0, j, y);
-            }
-        } else {
-            // visibilities in list order; each change of (footprint, w row)
-            // ends the run; invalid visibilities (key -1) add nothing
-#pragma unroll 1
-            for (int k = 0; k < 4; ++k) {
-                const int r = 8 * k + p;
-                const int kr = __shfl_sync(kFull, iA.key, r);
-                const int fr = __shfl_sync(kFull, iA.fw, r);
-                const int br = T2D ? __shfl_sync(kFull, iA.blk, r) : 0;
-                float2 y;
-                y.x = __shfl_sync(kFull, yA.x, r);
-                y.y = __shfl_sync(kFull, yA.y, r);
-                bool done = kr < 0;
-#pragma unroll 1
-                while (true) {
-                    const unsigned todo = __ballot_sync(kFull, !done);
-                    if (todo == 0)
-                        break;
-                    const int leader = __ffs(todo) - 1;
-                    const int lk = __shfl_sync(kFull, kr, leader);
-                    const int lf = __shfl_sync(kFull, fr, leader);
-                    if (lk != run_key || lf != run_fw) {
-                        if (run_key >= 0)
-                            flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
-                        run_key = lk;
-                        run_fw = lf;
-                    }
-                    const bool mine = !done && kr == lk && fr == lf;
-                    accumulate_vis<T2D>(T, S, g2, r, br, j, mine ? y : make_float2(0.f, 0.f));
-                    done = done || mine;
-                }
-            }
-        }
+        accumulate_half<T2D>(rs, ws, ws.st[sA][0], iA0, yA0, g, wtab, gwt, g2, p, j);
+        if (bA.n > kBatch)
+            accumulate_half<T2D>(rs, ws, ws.st[sA][1], iA1, yA1, g, wtab, gwt, g2, p, j);
         __syncwarp();
         stage ^= 1;
     }
-    if (run_key >= 0)
-        flush(T, ws, sub_s, run_key, run_fw, g, wtab, gwt, p, j);
+    if (rs.key >= 0)
+        flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
 }
 
 size_t smem_bytes(const degrid_plan *p)
