@@ -24,6 +24,7 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kSchedMaxS = 4096;            // subgrids the one-kernel schedule scans in shared memory
 constexpr int kSchedMaxBlocks = 1024;
+constexpr int kSchedThreads = 256;          // the one-kernel schedule's blocks
 
 // Exclusive scan of ceil(count_s / chunk) over s < S into pre[0..S] (shared
 // or global memory), each entry clamped to `capacity`; every thread of the
@@ -41,7 +42,8 @@ __device__ long long scan_chunks(const int64_t *__restrict__ offs, int S, int64_
             atomicOr(&status->flags, kFlagOffsets);
     }
     __syncthreads();
-    for (int base = 0; base < S; base += kScanThreads) {
+    const int nt = blockDim.x;              // a multiple of 32, at most kScanThreads
+    for (int base = 0; base < S; base += nt) {
         const int s = base + tid;
         long long cnt = 0;
         if (s < S) {
@@ -81,7 +83,7 @@ __device__ long long scan_chunks(const int64_t *__restrict__ offs, int S, int64_
             pre[s] = (int)min(before, (long long)capacity);
         __syncthreads();
         if (tid == 0)
-            carry_sh += warp_sums[kScanThreads / kWarp - 1];
+            carry_sh += warp_sums[nt / kWarp - 1];
         __syncthreads();
     }
     long long total = carry_sh;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void fill_chunks(const int *pre, const int64_t *__res
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kSchedThreads)
 chunk_schedule(const int64_t *__restrict__ offs, int S, int64_t n_vis, int chunk, int *__restrict__ n_chunks,
                int capacity, int *__restrict__ work_counter, DeviceStatus *__restrict__ status,
                ChunkDesc *__restrict__ chunks)
@@ -157,7 +159,7 @@ cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_s
 {
     if (n_subgrids <= kSchedMaxS) {
         const int blocks = n_subgrids < 1 ? 1 : (n_subgrids < kSchedMaxBlocks ? n_subgrids : kSchedMaxBlocks);
-        chunk_schedule<<<blocks, kScanThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, n_chunks,
+        chunk_schedule<<<blocks, kSchedThreads, 0, st>>>(vis_offsets, n_subgrids, n_vis, chunk, n_chunks,
                                                         capacity, work_counter, status, chunks);
         return cudaGetLastError();
     }
