@@ -1,6 +1,6 @@
-// TMA and mbarrier helpers shared by the kernels that copy whole footprints
-// into shared memory (the gather kernel; the staged M builds of the
-// degridding kernel).
+// TMA and mbarrier helpers of the kernels that move whole footprints between
+// the stack and shared memory (the gather kernel reads them, the scattered
+// gridding kernel adds them back).
 //
 // With nz = 4 a footprint row (8 columns x 4 samples) is one contiguous
 // piece of the stack: 256 bytes in complex64, 128 in FP16/BF16 code pairs.
