@@ -632,6 +632,47 @@ def run_ours(args, rank, world):
         mean_step, mean_kern = float(t[0]), float(t[1])
     value = world * w.n_vis / (mean_step * 1e-3)
 
+    # end to end through the C-ABI call on HOST buffers (degrid_execute_host),
+    # on every rank: the step's inputs cross the host link inside the timing
+    e2e = None
+    if not args.no_e2e:
+        h_sub = torch.empty(sub.shape, dtype=sub.dtype, pin_memory=True)
+        h_sub.copy_(torch.from_numpy(sub_np))
+        h_uvw = torch.empty(uvw.shape, dtype=uvw.dtype, pin_memory=True)
+        h_uvw.copy_(torch.from_numpy(w.uvw))
+        h_offs = torch.from_numpy(w.vis_offsets).pin_memory()
+        h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+
+        def e2e_run():
+            ts = []
+            for i in range(args.e2e_steps + 2):
+                flush.zero_()                   # no host line left in L2 from the last step
+                torch.cuda.synchronize()
+                if world > 1:
+                    torch.distributed.barrier()
+                t0 = time.perf_counter()
+                plan.degrid_host(h_sub, h_uvw, h_offs, out=h_out)
+                if i >= 2:
+                    ts.append(time.perf_counter() - t0)
+            assert plan.status() == 0
+            med = statistics.median(ts)
+            if world > 1:                       # the slowest rank sets the job's time
+                t = torch.tensor([med], dtype=torch.float64, device=dev)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                med = float(t[0])
+            return world * w.n_vis / med
+
+        # pinned buffers: the kernel reads them in place over the host link
+        e2e_value = e2e_run()
+        e2e_out = h_out.numpy().copy()
+        # the same call made to copy the inputs in subgrid groups instead
+        plan.set_host_direct(False)
+        h_out.zero_()
+        copy_value = e2e_run()
+        copy_out = h_out.numpy().copy()
+        plan.set_host_direct(True)
+        e2e = (h_sub, h_uvw, h_offs, h_out, e2e_value, copy_value, e2e_out, copy_out)
+
     if rank != 0:
         if world > 1:
             torch.distributed.barrier()
@@ -738,38 +779,12 @@ def run_ours(args, rank, world):
             del codes, scale
         line["precision_sweep"] = sweep
 
-    if not args.no_e2e:
-        # through the C-ABI call on HOST buffers (degrid_execute_host): the
-        # copies of each step's inputs and its output are inside the timing
-        h_sub = torch.empty(sub.shape, dtype=sub.dtype, pin_memory=True)
-        h_sub.copy_(torch.from_numpy(sub_np))
-        h_uvw = torch.empty(uvw.shape, dtype=uvw.dtype, pin_memory=True)
-        h_uvw.copy_(torch.from_numpy(w.uvw))
-        h_offs = torch.from_numpy(w.vis_offsets).pin_memory()
-        h_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
-        def e2e_run():
-            ts = []
-            for i in range(args.e2e_steps + 2):
-                flush.zero_()                   # no host line left in L2 from the last step
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                plan.degrid_host(h_sub, h_uvw, h_offs, out=h_out)
-                if i >= 2:
-                    ts.append(time.perf_counter() - t0)
-            assert plan.status() == 0
-            return w.n_vis / statistics.median(ts)
-
-        # pinned buffers: the kernel reads them in place over the host link
-        e2e_value = e2e_run()
-        e2e_err = sampled_error(h_out.numpy(), w, g_uv, g_w, sub_np)
-        # the same call made to copy the inputs in subgrid groups instead
-        plan.set_host_direct(False)
-        h_out.zero_()
-        copy_value = e2e_run()
-        copy_err = sampled_error(h_out.numpy(), w, g_uv, g_w, sub_np)
-        plan.set_host_direct(True)
-        bi = h_sub.numel() * h_sub.element_size() + h_uvw.numel() * 8 + h_offs.numel() * 8
-        bo = h_out.numel() * h_out.element_size()
+    if e2e is not None:
+        h_sub, h_uvw, h_offs, h_out, e2e_value, copy_value, e2e_out, copy_out = e2e
+        e2e_err = sampled_error(e2e_out, w, g_uv, g_w, sub_np)
+        copy_err = sampled_error(copy_out, w, g_uv, g_w, sub_np)
+        bi = world * (h_sub.numel() * h_sub.element_size() + h_uvw.numel() * 8 + h_offs.numel() * 8)
+        bo = world * h_out.numel() * h_out.element_size()
         line["e2e"] = {"value": e2e_value, "unit": UNIT,
                        "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo),
                        "rel_l2_vs_oracle": e2e_err[0],
@@ -777,7 +792,9 @@ def run_ours(args, rank, world):
                                "kernel loads the coordinates (%d B) and the footprint rows it "
                                "uses (%d touched elements, %d B of the %d B stack) over the host "
                                "link and stores the visibilities there; the offsets are copied. "
-                               "h2d_bytes_per_step counts every input the call is given"
+                               "h2d_bytes_per_step counts every input the call is given (all "
+                               "ranks); the value is all ranks' visibilities over the slowest "
+                               "rank's median step"
                                % (h_uvw.numel() * 8, touched, touched * 8,
                                   h_sub.numel() * h_sub.element_size()),
                        "copy_path": {"value": copy_value, "rel_l2_vs_oracle": copy_err[0],
