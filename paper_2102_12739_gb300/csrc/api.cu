@@ -200,6 +200,7 @@ static dg_status plan_create(degrid_plan_t *out, int nx, int ny, int nz, const d
                       const double *g_uv2, int uv_support, int uv_oversample, const double *g_w,
                       int w_support, int w_oversample, dg_dtype dtype, int device)
 {
+    NvtxRange nvtx_range("degrid_plan_create");
     if (!out)
         return DG_ERR_ARG;
     *out = nullptr;
@@ -494,6 +495,7 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
                          const float *subgrid_scale, const double *uvw,
                          const int64_t *vis_offsets, int64_t n_vis, float *vis_out)
 {
+    NvtxRange nvtx_range("degrid_execute");
     if (!p || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
     if (n_vis > 0 && (!uvw || !vis_out || !subgrids || n_subgrids == 0))
@@ -539,6 +541,7 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
                                const int64_t *vis_offsets, int64_t n_vis, const float *vis_in,
                                float *sub_out, int accumulate)
 {
+    NvtxRange nvtx_range("grid_adjoint_execute");
     if (!p || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
     if (n_subgrids > 0 && !sub_out)
@@ -587,6 +590,7 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
 dg_status degrid_coords_execute(degrid_plan_t p, void *stream, const double *uvw, int64_t n_vis,
                                 int32_t *coords_out)
 {
+    NvtxRange nvtx_range("degrid_coords_execute");
     if (!p || n_vis < 0)
         return DG_ERR_ARG;
     if (n_vis > 0 && (!uvw || !coords_out))

@@ -223,6 +223,7 @@ extern "C" dg_status degrid_execute_host(degrid_plan_t p, int n_subgrids, const 
                                          const float *subgrid_scale, const double *uvw,
                                          const int64_t *vis_offsets, int64_t n_vis, float *vis_out)
 {
+    NvtxRange nvtx_range("degrid_execute_host");
     if (!p || n_subgrids < 0 || n_vis < 0 || !vis_offsets)
         return DG_ERR_ARG;
     if (n_vis > 0 && (!uvw || !vis_out || !subgrids || n_subgrids == 0))

@@ -258,6 +258,19 @@ struct degrid_plan {
 
 void dg_free_host_exec(degrid_plan *p);   // host_exec.cu
 
+#include <nvtx3/nvToolsExt.h>
+
+// An NVTX range over an entry point (plan creation, the execute calls), so
+// profilers show the library's calls around its kernels; free when no tool
+// is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+
 // Kernel launchers (one per translation unit).
 cudaError_t dg_launch_degrid(degrid_plan *p, cudaStream_t st, const void *subgrids,
                              const float *scale, const double *uvw,

@@ -84,6 +84,7 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
                                             const int64_t *vis_offsets, int64_t n_vis,
                                             float *vis_out, unsigned long long *status_out)
 {
+    NvtxRange nvtx_range("degrid_execute_noalloc");
     if (nx < 8 || ny < 8 || nz < 4 || (int64_t)nx * ny * nz >= ((int64_t)1 << 31))
         return DG_ERR_ARG;
     if (dtype != DG_C64 && dtype != DG_C32_F16 && dtype != DG_C32_BF16)
