@@ -60,7 +60,8 @@ typedef enum {
     DG_ERR_OFFSETS = 5,        /* vis_offsets malformed (found on the device) */
     DG_ERR_UNSUPPORTED = 6,    /* GCF support / subgrid shape not supported */
     DG_ERR_SCRATCH_LIMIT = 7,  /* sizes exceed the fixed scratch of degrid_execute_noalloc */
-    DG_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up (found on the device) */
+    DG_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up (found on the device) */
+    DG_ERR_BOUNDS = 9          /* an index check of the bounds-checking build failed (on the device) */
 } dg_status;
 
 /* Subgrid storage: complex64, or FP16 / BF16 (re, im) pairs with one FP32
@@ -366,8 +367,10 @@ dg_status degrid_pack_subgrids(void *stream, dg_dtype dtype, int n_subgrids, int
  * stores the number of invalid visibilities seen since the last call in
  * *n_invalid (may be NULL) and returns DG_ERR_TIMEOUT if a bounded wait of
  * a kernel gave up (the gather kernel's waits on its copies; the results of
- * that call are incomplete), else DG_ERR_OFFSETS if a call saw malformed
- * vis_offsets, else DG_OK (or DG_ERR_CUDA).
+ * that call are incomplete), else DG_ERR_BOUNDS if the library was built
+ * with DEGRID_BOUNDS_CHECK and an index the coordinate step produced fell
+ * outside its buffer (that visibility was skipped), else DG_ERR_OFFSETS if a
+ * call saw malformed vis_offsets, else DG_OK (or DG_ERR_CUDA).
  */
 dg_status degrid_get_status(degrid_plan_t plan, void *stream, int64_t *n_invalid);
 

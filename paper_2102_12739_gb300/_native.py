@@ -22,6 +22,7 @@ DG_ERR_OFFSETS = 5
 DG_ERR_UNSUPPORTED = 6
 DG_ERR_SCRATCH_LIMIT = 7
 DG_ERR_TIMEOUT = 8
+DG_ERR_BOUNDS = 9
 
 DG_C64 = 0
 DG_C32_F16 = 1
@@ -77,8 +78,17 @@ class DegridError(RuntimeError):
         super().__init__(f"{where}: {status_string(status)} (status {status})")
 
 
+def _variant() -> str:
+    """The library variant named by $DEGRID_LIBRARY_VARIANT ("" = the product library)."""
+    v = os.environ.get("DEGRID_LIBRARY_VARIANT", "")
+    if v and v not in _build.VARIANTS:
+        raise RuntimeError(f"unknown DEGRID_LIBRARY_VARIANT {v!r}; known: {sorted(_build.VARIANTS)}")
+    return v
+
+
 def lib_path() -> str:
-    return _build.LIB_PATH
+    v = _variant()
+    return _build.variant_path(v) if v else _build.LIB_PATH
 
 
 def load(build_if_missing: bool = True):
@@ -86,8 +96,12 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB_PATH
-            if build_if_missing and not _build.up_to_date():
+            variant = _variant()
+            path = lib_path()
+            if variant:
+                if build_if_missing:
+                    _build.build_variant(variant)
+            elif build_if_missing and not _build.up_to_date():
                 _build.build()
             if not os.path.exists(path):
                 raise RuntimeError(f"libdegrid.so not found at {path}; run "

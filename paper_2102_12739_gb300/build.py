@@ -83,6 +83,48 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     return LIB_PATH
 
 
+# Library variants built beside the product library, each in _build/<name>/:
+# "bounds" checks every index the coordinate step produces (footprint start,
+# GCF rows, 2D weight block, copy-engine box) against the buffers' extents
+# and reports a violation through degrid_get_status (DG_ERR_BOUNDS) instead
+# of touching memory; the index-safety check the GPU tests run against.
+VARIANTS = {"bounds": ("DEGRID_BOUNDS_CHECK",)}
+
+
+def variant_path(name: str) -> str:
+    return os.path.join(OUT_DIR, name, "libdegrid.so")
+
+
+def build_variant(name: str, force: bool = False) -> str:
+    """Compile and link the library variant `name` if it is missing or stale."""
+    defines = VARIANTS[name]
+    path = variant_path(name)
+    if not force and os.path.exists(path) and all(os.path.getmtime(f) <= os.path.getmtime(path)
+                                                  for f in _inputs()):
+        return path
+    out = os.path.dirname(path)
+    os.makedirs(out, exist_ok=True)
+    cc = nvcc()
+    flags = [f"-D{d}" for d in defines]
+
+    def compile_one(src):
+        obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
+        r = subprocess.run([cc, *ARCH, *NVCC_FLAGS, *flags, "-c", os.path.join(CSRC, src), "-o", obj],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = path + ".tmp%d" % os.getpid()
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, path)
+    return path
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")

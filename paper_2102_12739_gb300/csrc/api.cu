@@ -188,6 +188,7 @@ const char *degrid_status_string(dg_status status)
     case DG_ERR_UNSUPPORTED: return "unsupported GCF support or subgrid shape";
     case DG_ERR_SCRATCH_LIMIT: return "sizes exceed the fixed scratch of degrid_execute_noalloc";
     case DG_ERR_TIMEOUT: return "a bounded device-side wait gave up; results are incomplete";
+    case DG_ERR_BOUNDS: return "an index check of the bounds-checking build failed";
     }
     return "unknown status";
 }
@@ -645,6 +646,8 @@ dg_status degrid_get_status(degrid_plan_t p, void *stream, int64_t *n_invalid)
         *n_invalid = (int64_t)h.n_invalid;
     if (h.flags & dg::kFlagTimeout)
         return DG_ERR_TIMEOUT;
+    if (h.flags & dg::kFlagBounds)
+        return DG_ERR_BOUNDS;
     return (h.flags & (dg::kFlagOffsets | dg::kFlagCapacity)) ? DG_ERR_OFFSETS : DG_OK;
 }
 

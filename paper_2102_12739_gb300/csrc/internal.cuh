@@ -164,6 +164,24 @@ struct DeviceStatus {
 constexpr unsigned long long kFlagOffsets = 1ull;
 constexpr unsigned long long kFlagCapacity = 2ull;
 constexpr unsigned long long kFlagTimeout = 4ull;   // a bounded device wait gave up
+constexpr unsigned long long kFlagBounds = 8ull;    // an index check failed (DEGRID_BOUNDS_CHECK builds)
+
+#ifdef DEGRID_BOUNDS_CHECK
+// Index checks of the bounds-checking build: every index the coordinate step
+// produces for a valid visibility against the extents of what it addresses.
+// A failure records kFlagBounds; the caller then treats the visibility as
+// invalid, so nothing is read or written through the bad index.
+__device__ __forceinline__ bool indices_in_bounds(int key, int fu, int fv, int fw, const Geometry &g,
+                                                  DeviceStatus *status)
+{
+    const int64_t last = (int64_t)key + (int64_t)(kUV - 1) * g.row_stride + (int64_t)(kUV - 1) * g.nz + (kW - 1);
+    const bool ok = key >= 0 && last < g.plane && (unsigned)fu < (1u << g.log2_uv_os) &&
+                    (unsigned)fv < (1u << g.log2_uv_os) && (unsigned)fw < (1u << g.log2_w_os);
+    if (!ok)
+        atomicOr(&status->flags, kFlagBounds);
+    return ok;
+}
+#endif
 
 // Work decomposition: chunk k covers the n visibilities [lo, lo + n) of
 // subgrid s (n <= chunk size; a chunk never straddles two subgrids).

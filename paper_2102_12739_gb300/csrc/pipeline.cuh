@@ -209,7 +209,11 @@ __device__ __forceinline__ Issued issue_rows(const Batch &b, const Coords3 &c, c
 {
     const bool in = lane < b.n;
     VisCoords vc;
-    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
+    bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
+#ifdef DEGRID_BOUNDS_CHECK
+    if (valid)
+        valid = indices_in_bounds((vc.y0 * g.nx + vc.x0) * g.nz + vc.z0, vc.fu, vc.fv, vc.fw, g, status);
+#endif
     Issued r;
     r.key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
     r.fw = valid ? vc.fw : 0;

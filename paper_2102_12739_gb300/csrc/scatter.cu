@@ -67,7 +67,11 @@ __device__ __forceinline__ void snap_scatter(ScatterIssue &is, const Coords3 &c,
 {
     const bool in = lane < is.b.n;
     VisCoords vc;
-    const bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
+    bool valid = in && visibility_coords(c.u, c.v, c.w, g, vc);
+#ifdef DEGRID_BOUNDS_CHECK
+    if (valid)
+        valid = indices_in_bounds((vc.y0 * g.nx + vc.x0) * g.nz + vc.z0, vc.fu, vc.fv, vc.fw, g, status);
+#endif
     is.key = valid ? (vc.y0 * g.nx + vc.x0) * g.nz + vc.z0 : -1;
     is.fw = valid ? vc.fw : 0;
     is.fu = valid ? vc.fu : 0;

@@ -96,3 +96,22 @@ def test_header_constants_match_the_binding():
         assert m and int(m.group(1)) == getattr(_native, name)
     assert re.search(r"#define\s+DG_DIRECT_RUNS_DEFAULT\s+DG_DIRECT_RUNS_NEVER", text)
     assert _native.DG_DIRECT_RUNS_DEFAULT == _native.DG_DIRECT_RUNS_NEVER
+
+
+def test_library_variant_selection():
+    # DEGRID_LIBRARY_VARIANT picks a variant build (the bounds-checking one);
+    # an unknown name is refused; the product library is the default
+    import subprocess
+    import sys
+    code = ("import paper_2102_12739_gb300._native as n; print(n.lib_path())")
+    env = dict(os.environ, DEGRID_LIBRARY_VARIANT="bounds")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         cwd=ROOT, check=True).stdout.strip()
+    assert out == build.variant_path("bounds") and "/bounds/" in out
+    env["DEGRID_LIBRARY_VARIANT"] = "nonsense"
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert r.returncode != 0 and "unknown DEGRID_LIBRARY_VARIANT" in r.stderr
+    env.pop("DEGRID_LIBRARY_VARIANT")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         cwd=ROOT, check=True).stdout.strip()
+    assert out == build.LIB_PATH
