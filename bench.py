@@ -738,7 +738,10 @@ def run_ours(args, rank, world):
         "wall_s_timed_region": wall,
     }
 
-    if not args.no_sweep:
+    # the single-GPU diagnostics (storage sweep, other workloads, the CPU
+    # oracle) run at N = 1 only: at N > 1 they would hold every GPU meanwhile
+    solo = world == 1
+    if solo and not args.no_sweep:
         # config 3: each storage type, plain and with the compensated reduction; errors
         # against the FP64 oracle on the original complex64 subgrids (quantisation
         # included) and, for FP16/BF16, on the values the kernel reads (kernel error)
@@ -808,24 +811,25 @@ def run_ours(args, rank, world):
                        "host_link": "about 211 GB/s host to device on this box, for copies "
                                     "and for kernel loads alike"}
 
-    if not args.no_adjoint:
+    if solo and not args.no_adjoint:
         line["adjoint"] = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)
 
-    line["latency"] = latency_section(torch, dg, synth, dev, args.aux_steps)
+    if solo:
+        line["latency"] = latency_section(torch, dg, synth, dev, args.aux_steps)
 
-    if not args.no_table2d:
+    if solo and not args.no_table2d:
         line["table2d"] = table2d_section(torch, dg, synth, dev, flush, args.aux_steps, sub, sub_np,
                                           uvw, offs, w)
 
-    if not args.no_scatter:
+    if solo and not args.no_scatter:
         line["scatter"] = scatter_section(torch, dg, synth, dev, flush, args.aux_steps,
                                           dg.measure_l2_read_bw(local))
 
-    if not args.no_batched:
+    if solo and not args.no_batched:
         del sub_np
         line["batched"] = batched_section(torch, dg, synth, dev, flush, args.aux_steps)
 
-    if not args.no_cpu_baseline:
+    if solo and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g_uv, g_w)
 
     print(json.dumps(line), flush=True)
