@@ -293,10 +293,7 @@ def batched_section(torch, dg, synth, dev, flush, steps):
     for each storage type autotuned, captured once in a CUDA graph and
     replayed."""
     w = synth.workload("batched512")
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(0)
-    sub = torch.randn((w.n_subgrids,) + w.shape + (2,), generator=gen, device=dev,
-                      dtype=torch.float32).view(torch.complex64)[..., 0].contiguous()
+    sub = synth.subgrid_stack_on_device(w.n_subgrids, dev, w.shape)
     uvw = torch.from_numpy(w.uvw).to(dev)
     offs = torch.from_numpy(w.vis_offsets).to(dev)
     out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
@@ -492,10 +489,7 @@ def adjoint_section(torch, dg, synth, dev, flush, steps):
         assert plan.status() == 0
         # the same workload forward (degridding) and as one autograd step:
         # forward, loss ||D s - y||^2, backward (gridding of 2 (D s - y))
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(0)
-        sub = torch.randn((w.n_subgrids,) + w.shape + (2,), generator=gen, device=dev,
-                          dtype=torch.float32).view(torch.complex64)[..., 0].contiguous()
+        sub = synth.subgrid_stack_on_device(w.n_subgrids, dev, w.shape)
         vis = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
 
         def fwd():

@@ -195,8 +195,10 @@ dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
  * tensor reduce-add of the copy engine, instead of the run accumulation
  * with float2 atomics (FP32 additions in another order: the last bits
  * differ).  Needs nz = 4 and a separable G_uv table: enabling it on another
- * plan returns DG_ERR_UNSUPPORTED.  Returns DG_OK, DG_ERR_ARG (enabled not
- * 0 / 1) or DG_ERR_UNSUPPORTED.
+ * plan returns DG_ERR_UNSUPPORTED.  Calls whose stack has more than
+ * 2^31 - 1 rows in all (n_subgrids * ny) take the footprint-cache kernels
+ * whatever the setting (the copy engine's row coordinate is 32-bit).
+ * Returns DG_OK, DG_ERR_ARG (enabled not 0 / 1) or DG_ERR_UNSUPPORTED.
  */
 dg_status degrid_plan_set_gather(degrid_plan_t plan, int enabled);
 dg_status degrid_plan_get_gather(degrid_plan_t plan, int *enabled);

@@ -155,6 +155,14 @@ struct KernelTimer {
     }
 };
 
+// The gather and scatter kernels address the stack as one 2D tensor of
+// n_subgrids * ny rows with 32-bit row coordinates; past that the plan takes
+// the footprint-cache kernels (the same results, bit for bit).
+bool tma_rows_fit(const degrid_plan *p, int n_subgrids)
+{
+    return (int64_t)n_subgrids * p->geo.ny <= (int64_t)0x7fffffff;
+}
+
 // Persistent grid: the resident CTAs of every SM, but no more CTAs than
 // there are chunks for their chunk-claiming warps.
 int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int chunk, int max_per_sm, int claimers_per_block)
@@ -521,7 +529,7 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
-    if (p->gather) {
+    if (p->gather && tma_rows_fit(p, n_subgrids)) {
         // one CTA per SM
         const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, 1, dg_gather_warps(p->dtype));
         KernelTimer timer(p, s);
@@ -571,7 +579,7 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
-    if (p->gather && aligned(sub_out, 16)) {
+    if (p->gather && aligned(sub_out, 16) && tma_rows_fit(p, n_subgrids)) {
         // scattered coverage: every visibility's tile added by a tensor reduce, one CTA per SM
         const int blocks = grid_blocks(p, n_subgrids, n_vis, chunk, 1, dg_scatter_warps());
         KernelTimer timer(p, s);

@@ -347,3 +347,58 @@ def workload(name: str) -> Workload:
     if name == "scatter16_250k":
         return scattered_workload(name, [250_000] * 16)
     raise KeyError(name)
+
+
+# ---- inputs generated on the device ----------------------------------------
+# For sizes the host should not hold (stacks of thousands of subgrids, more
+# than 2^31 visibilities).  The values are inputs like the rest: tests copy
+# the rows and subgrids they check back to the host and hand them to the
+# oracle.  torch is imported here only, so the module stays numpy-only for
+# the oracle's users.
+
+def subgrid_stack_on_device(n_subgrids: int, device, shape=SUBGRID_SHAPE, seed: int = SEED_SUBGRID):
+    """complex64 [S][ny][nx][nz] on `device`, i.i.d. complex Gaussian (torch's
+    generator for that device, seeded)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    return torch.randn((n_subgrids,) + tuple(shape) + (2,), generator=gen, device=device,
+                       dtype=torch.float32).view(torch.complex64)[..., 0].contiguous()
+
+
+_SLAB = 1 << 27     # rows per temporary: 1 GiB of float64
+
+
+def fill_line_on_device(uvw, lo: int, n: int, start, end) -> None:
+    """Rows [lo, lo + n) of the device tensor uvw (float64 [N][3]) := the line
+    start + j * step, step = (end - start) / (n - 1), as in `line`."""
+    import torch
+    step = [(float(e) - float(s)) / max(n - 1, 1) for s, e in zip(start, end)]
+    for a in range(0, n, _SLAB):
+        m = min(_SLAB, n - a)
+        j = torch.arange(a, a + m, dtype=torch.float64, device=uvw.device)
+        for k in range(3):
+            uvw[lo + a: lo + a + m, k] = j * step[k] + float(start[k])
+
+
+def fill_scattered_on_device(uvw, lo: int, n: int, shape=SUBGRID_SHAPE, seed: int = SEED_UVW) -> None:
+    """Rows [lo, lo + n) of uvw := points uniform in the valid box, as in
+    `scattered_list` (torch's generator for the device, seeded)."""
+    import torch
+    ny, nx, _ = shape
+    box = (uv_box(nx), uv_box(ny), (W_LO, W_HI))
+    gen = torch.Generator(device=uvw.device)
+    gen.manual_seed(seed)
+    for a in range(0, n, _SLAB):
+        m = min(_SLAB, n - a)
+        r = torch.rand((m, 3), dtype=torch.float64, device=uvw.device, generator=gen)
+        for k in range(3):
+            r[:, k] = r[:, k] * (box[k][1] - box[k][0]) + box[k][0]
+        uvw[lo + a: lo + a + m] = r
+
+
+def random_line_on_device(uvw, lo: int, n: int, rng, shape=SUBGRID_SHAPE) -> None:
+    """Rows [lo, lo + n) of uvw := a line with random ends, as in `random_line`."""
+    start = _uniform_point(rng, shape)
+    end = _uniform_point(rng, shape)
+    fill_line_on_device(uvw, lo, n, start, end)
