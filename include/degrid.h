@@ -39,6 +39,10 @@
  *    degrid_get_status.  No entry point traps or asserts on the device.
  *  - A plan is bound to one device and is not thread-safe: calls on one plan
  *    must not run concurrently from several host threads.
+ *  - Calls on one plan share its device scratch (chunk table, claim counter,
+ *    status): they must reach the device in order, so issue them on one
+ *    stream or order their streams with events.  For work in flight on
+ *    several streams at once, use one plan per stream (plans share nothing).
  */
 #ifndef DEGRID_H
 #define DEGRID_H
