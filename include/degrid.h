@@ -133,7 +133,13 @@ void degrid_plan_destroy(degrid_plan_t plan);
  * tunes N_b, the visibilities per thread block, by hand; Section "Results").
  *   chunk            visibilities per work item claimed by one warp
  *                    (multiple of 32, 32 .. 65536); a work item never
- *                    straddles two subgrids
+ *                    straddles two subgrids.  Every item is one atomic
+ *                    claim on a single device-wide counter: items of
+ *                    fewer than 64 visibilities (one pipeline step) make
+ *                    every step a claim and the counter then bounds the
+ *                    call (gridding measured 18x slower at 32 than at
+ *                    256); 128 .. 1024 is the useful range, the one the
+ *                    autotuner searches
  *   warps_per_block  warps per CTA (1 .. 32)
  *   blocks_per_sm    resident CTAs per SM for the persistent grid
  *                    (0 = as many as the occupancy calculator allows)
