@@ -270,6 +270,13 @@ size_t smem_bytes(const degrid_plan *p)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)p->warps_per_block;
 }
 
+// Dynamic shared memory opened so far for the plan's kernel instance on its device.
+std::atomic<size_t> &smem_record(const degrid_plan *p)
+{
+    static std::atomic<size_t> table[2][kMaxDevices];
+    return dg_smem_record(table[p->guv2 ? 1 : 0], p->device);
+}
+
 }  // namespace
 }  // namespace dg
 
@@ -282,16 +289,9 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
     Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const size_t smem = smem_bytes(p);
     auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
-    // the dynamic shared-memory limit is set once per device, instance and size
-    static size_t smem_set[2][kMaxDevices] = {};
-    size_t *set = &smem_set[p->guv2 ? 1 : 0][p->device < kMaxDevices ? p->device : 0];
-    if (p->device >= kMaxDevices || *set != smem) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        if (p->device < kMaxDevices)
-            *set = smem;
-    }
+    const cudaError_t e = dg_open_smem(smem_record(p), kernel, smem);
+    if (e != cudaSuccess)
+        return e;
     return launch_pdl(kernel, dim3(grid_blocks), dim3(p->warps_per_block * kWarp), smem, st, p->geo, uvw,
                       reinterpret_cast<const float2 *>(vis_in), (const float *)p->guv, (const float *)p->gw,
                       sched, reinterpret_cast<float2 *>(sub_out), p->status, (const float *)p->guv2);
@@ -303,7 +303,7 @@ int dg_max_blocks_per_sm_adjoint(degrid_plan *p)
     int n = 0;
     const size_t smem = smem_bytes(p);
     auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (dg_open_smem(smem_record(p), kernel, smem) != cudaSuccess)
         return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, p->warps_per_block * kWarp, smem) !=
         cudaSuccess)

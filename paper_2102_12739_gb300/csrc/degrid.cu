@@ -462,22 +462,24 @@ size_t smem_bytes(const degrid_plan *p, int warps)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)warps;
 }
 
+// Dynamic shared memory opened so far for a kernel instance on a device.
+template <int DT, bool COMP, bool DIRECT, bool T2D>
+std::atomic<size_t> &smem_record(int device)
+{
+    static std::atomic<size_t> table[kMaxDevices];
+    return dg_smem_record(table, device);
+}
+
 template <int DT, bool COMP, bool DIRECT, bool T2D>
 cudaError_t launch(degrid_plan *p, cudaStream_t st, const void *subgrids, const float *scale,
                    const double *uvw, float2 *out, const Schedule &sched, int grid_blocks)
 {
     const int threads = p->warps_per_block * kWarp;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    // the dynamic shared-memory limit is set once per device and size
-    static size_t smem_set[kMaxDevices] = {};
-    if (p->device >= kMaxDevices || smem_set[p->device] != smem) {
-        cudaError_t e = cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        if (p->device < kMaxDevices)
-            smem_set[p->device] = smem;
-    }
+    cudaError_t e = dg_open_smem(smem_record<DT, COMP, DIRECT, T2D>(p->device), degrid_kernel<DT, COMP, DIRECT, T2D>,
+                                 smem);
+    if (e != cudaSuccess)
+        return e;
     // 16-byte footprint loads need an aligned stack and nz a multiple of the
     // elements per 16 bytes
     const bool vec_ok = (reinterpret_cast<uintptr_t>(subgrids) & 15) == 0 &&
@@ -492,8 +494,8 @@ int max_blocks(degrid_plan *p)
 {
     int n = 0;
     const size_t smem = smem_bytes(p, p->warps_per_block);
-    if (cudaFuncSetAttribute(degrid_kernel<DT, COMP, DIRECT, T2D>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (dg_open_smem(smem_record<DT, COMP, DIRECT, T2D>(p->device), degrid_kernel<DT, COMP, DIRECT, T2D>, smem) !=
+        cudaSuccess)
         return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, degrid_kernel<DT, COMP, DIRECT, T2D>,
                                                       p->warps_per_block * kWarp, smem) != cudaSuccess)

@@ -325,17 +325,12 @@ cudaError_t launch_gather(degrid_plan *p, cudaStream_t st, const void *subgrids,
 {
     constexpr int kWarps = GatherShape<DT>::kWarps;
     const size_t smem = gather_smem(p, kWarps, sizeof(GatherSlot<DT>));
-    static size_t smem_set[kMaxDevices] = {};
-    if (p->device >= kMaxDevices || smem_set[p->device] != smem) {
-        cudaError_t e = cudaFuncSetAttribute(degrid_gather_kernel<DT, COMP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        if (p->device < kMaxDevices)
-            smem_set[p->device] = smem;
-    }
+    static std::atomic<size_t> smem_table[kMaxDevices];
+    cudaError_t e = dg_open_smem(dg_smem_record(smem_table, p->device), degrid_gather_kernel<DT, COMP>, smem);
+    if (e != cudaSuccess)
+        return e;
     CUtensorMap map;
-    cudaError_t e = encode_footprint_map<DT>(p, subgrids, n_subgrids, &map);
+    e = encode_footprint_map<DT>(p, subgrids, n_subgrids, &map);
     if (e != cudaSuccess)
         return e;
     return launch_pdl(degrid_gather_kernel<DT, COMP>, dim3(grid_blocks), dim3(kWarps * kWarp), smem, st,

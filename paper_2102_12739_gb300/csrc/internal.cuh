@@ -1,6 +1,9 @@
 // Internal definitions shared by the CUDA translation units of the library.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -275,6 +278,37 @@ struct degrid_plan {
 };
 
 void dg_free_host_exec(degrid_plan *p);   // host_exec.cu
+
+// Dynamic shared memory of a kernel instance beyond the default limit
+// (cudaFuncSetAttribute, per device).  `rec` (one per instance and device)
+// holds the largest size opened so far and the attribute only grows, so the
+// launches and occupancy queries of plans of different sizes, also from
+// several host threads, never find it below what they asked for.
+template <class F>
+cudaError_t dg_open_smem(std::atomic<size_t> &rec, F *func, size_t smem)
+{
+    if (rec.load(std::memory_order_acquire) >= smem)
+        return cudaSuccess;
+    static std::mutex m;
+    std::lock_guard<std::mutex> lock(m);
+    if (rec.load(std::memory_order_relaxed) >= smem)
+        return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        rec.store(smem, std::memory_order_release);
+    return e;
+}
+
+// The record of device `device` in a per-instance table (devices past the
+// table share a scratch record that never skips the call).
+inline std::atomic<size_t> &dg_smem_record(std::atomic<size_t> (&table)[dg::kMaxDevices], int device)
+{
+    static thread_local std::atomic<size_t> scratch;
+    if (device >= 0 && device < dg::kMaxDevices)
+        return table[device];
+    scratch.store(0);
+    return scratch;
+}
 
 #include <nvtx3/nvToolsExt.h>
 

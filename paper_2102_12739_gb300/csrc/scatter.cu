@@ -236,14 +236,11 @@ cudaError_t dg_launch_scatter(degrid_plan *p, cudaStream_t st, int n_subgrids, c
     using namespace dg;
     Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const size_t smem = wtable_bytes_host(p->geo) + sizeof(ScatterSlot) * 2 * (size_t)kSWarps;
-    static size_t smem_set[kMaxDevices] = {};
-    if (p->device >= kMaxDevices || smem_set[p->device] != smem) {
-        cudaError_t e = cudaFuncSetAttribute(grid_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    static std::atomic<size_t> smem_table[kMaxDevices];
+    {
+        const cudaError_t e = dg_open_smem(dg_smem_record(smem_table, p->device), grid_scatter_kernel, smem);
         if (e != cudaSuccess)
             return e;
-        if (p->device < kMaxDevices)
-            smem_set[p->device] = smem;
     }
     // the output stack as a 2D tensor [S * ny rows][2 nx nz floats]; a box is one footprint
     CUtensorMap map;

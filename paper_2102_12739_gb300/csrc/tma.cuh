@@ -87,16 +87,19 @@ __device__ __forceinline__ void fence_mbarrier_init()
 inline cudaError_t encode_2d(CUtensorMap *map, void *base, CUtensorMapDataType type, uint64_t dim0,
                              uint64_t dim1, uint64_t stride, uint32_t box0, uint32_t box1)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // looked up once (a function-local static: initialised once, also under
+    // concurrent first calls from several host threads)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
         const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                                cudaEnableDefault, &q);
-        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return e != cudaSuccess ? e : cudaErrorNotSupported;
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+        return e == cudaSuccess && q == cudaDriverEntryPointSuccess
+                   ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)
+                   : nullptr;
+    }();
+    if (!encode)
+        return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)dim0, (cuuint64_t)dim1};
     const cuuint64_t strides[1] = {(cuuint64_t)stride};
     const cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};

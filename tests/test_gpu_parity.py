@@ -747,3 +747,43 @@ def test_two_plans_on_two_streams_in_flight_at_once():
             assert torch.equal(torch.view_as_real(g).view(torch.int32), torch.view_as_real(r).view(torch.int32))
         # the gridding adds with atomics: the order of the FP32 additions varies
         assert rel_l2(ga.cpu().numpy(), gref) <= 1e-6
+
+
+def test_plans_of_different_sizes_from_several_host_threads():
+    # plans are independent: four host threads, each with its own plan and
+    # stream, CTAs of different sizes (so different shared-memory sizes of one
+    # kernel instance) and one on the gather kernel, call at the same time;
+    # every result matches the single-threaded one bit for bit
+    import threading
+    d = dev()
+    w = small_workload([2000, 700, 0, 1500], kind="mixed", seed=97)
+    sub, uvw, offs = upload(w, synth.subgrid_stack(4, seed=98))
+    with dg.DegridPlan(device=d) as p0:
+        ref = p0.degrid(sub, uvw, offs).cpu()
+    torch.cuda.synchronize()
+    errors, outs = [], {}
+
+    def worker(tag, warps, gather):
+        try:
+            torch.cuda.set_device(d)
+            s = torch.cuda.Stream(d)
+            with dg.DegridPlan(device=d, gather=gather) as p, torch.cuda.stream(s):
+                p.set_tuning(256, warps, 0)
+                res = [p.degrid(sub, uvw, offs) for _ in range(20)]
+                s.synchronize()
+                assert p.status() == 0
+                outs[tag] = [r.cpu() for r in res]
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k, warps, gather))
+               for k, (warps, gather) in enumerate([(2, False), (8, False), (4, False), (8, True)])]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert len(outs) == len(threads)
+    for res in outs.values():
+        for r in res:
+            assert torch.equal(torch.view_as_real(r).view(torch.int32), torch.view_as_real(ref).view(torch.int32))
