@@ -1,9 +1,6 @@
 // Internal definitions shared by the CUDA translation units of the library.
 #pragma once
 
-#include <atomic>
-#include <mutex>
-
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -278,6 +275,9 @@ struct degrid_plan {
 };
 
 void dg_free_host_exec(degrid_plan *p);   // host_exec.cu
+
+#include <atomic>
+#include <mutex>
 
 // Dynamic shared memory of a kernel instance beyond the default limit
 // (cudaFuncSetAttribute, per device).  `rec` (one per instance and device)
