@@ -341,9 +341,13 @@ class DegridPlan:
         """int32 [N, 6] = (x0, y0, z0, fu, fv, fw), -1 rows for invalid."""
         torch = _torch()
         _need(uvw, "uvw", torch.float64, self.device)
+        if uvw.dim() != 2 or uvw.shape[1] != 3:
+            raise ValueError("uvw must be [N, 3] float64")
         n = uvw.shape[0]
         if out is None:
             out = torch.empty((n, 6), dtype=torch.int32, device=self.device)
+        else:
+            _need(out, "out", torch.int32, self.device, (n, 6))
         st = load().degrid_coords_execute(self.handle, _stream_handle(stream, self.device),
                                           _vp(uvw), n, _vp(out))
         check(st, "degrid_coords_execute")

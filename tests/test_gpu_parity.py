@@ -561,6 +561,25 @@ def test_argument_errors_raise(plan):
         with pytest.raises(ValueError):
             p.degrid(torch.zeros((1,) + SHAPE + (2,), dtype=torch.bfloat16, device=d), uvw,
                      torch.tensor([0, 4], dtype=torch.int64, device=d))
+    # outputs and inputs of the wrong size are refused on the host, before
+    # anything is launched (a short buffer would be written past its end)
+    offs = torch.tensor([0, 4], dtype=torch.int64, device=d)
+    y = torch.zeros(4, dtype=torch.complex64, device=d)
+    bad_calls = [
+        lambda: plan.degrid(sub, uvw, offs, out=torch.empty(3, dtype=torch.complex64, device=d)),
+        lambda: plan.degrid(sub, uvw, offs, out=torch.empty(4, dtype=torch.float32, device=d)),
+        lambda: plan.grid(y, uvw, offs, 1, out=torch.empty((1, 8, 8, 4), dtype=torch.complex64, device=d)),
+        lambda: plan.grid(y[:3], uvw, offs, 1),
+        lambda: plan.coords(uvw, out=torch.empty((3, 6), dtype=torch.int32, device=d)),
+        lambda: plan.coords(uvw, out=torch.empty((4, 6), dtype=torch.int64, device=d)),
+        lambda: plan.coords(uvw.flatten()),
+        lambda: plan.degrid_host(sub.cpu(), uvw.cpu(), offs.cpu(), out=torch.empty(3, dtype=torch.complex64)),
+        lambda: dg.pack_subgrids(sub.real.contiguous(), "bf16"),
+    ]
+    for k, call in enumerate(bad_calls):
+        with pytest.raises((TypeError, ValueError)):
+            call()
+    assert plan.status() == 0
 
 
 def test_cuda_graph_replay_is_identical(plan):
