@@ -330,6 +330,7 @@ def workload(name: str) -> Workload:
                    throughput workload
     lines16_250k   its first 16 subgrids (4M visibilities; profiling case)
     batched512     512 subgrids, log-uniform counts in [1e3, 1e6]
+    batched64      64 subgrids of the same recipe (profiling case)
     diff32_100k    32 subgrids, 100,000 visibilities each (adjoint)
     scatter16_250k 16 subgrids, 250,000 scattered visibilities each (4M; no
                    footprint shared by consecutive visibilities)
@@ -342,6 +343,8 @@ def workload(name: str) -> Workload:
         return lines_workload(name, [250_000] * 16)
     if name == "batched512":
         return batched_workload(name, 512)
+    if name == "batched64":
+        return batched_workload(name, 64)
     if name == "diff32_100k":
         return lines_workload(name, [100_000] * 32)
     if name == "scatter16_250k":
