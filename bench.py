@@ -47,7 +47,7 @@ FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 
 TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
                           "paper_2102_12739_gb300/csrc/pipeline.cuh",
                           "paper_2102_12739_gb300/csrc/internal.cuh")
-TRAFFIC_SHA = "99f3040cb898e503"
+TRAFFIC_SHA = "d5cd8f28142fceec"
 TRAFFIC_BYTES_PER_VIS = (98.469120e6 + 11.723520e6) / 4_000_000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20

@@ -108,7 +108,7 @@ int call_chunk(const degrid_plan *p, int64_t n_vis)
 // capturing.
 dg_status ensure_capacity(degrid_plan *p, int S, int64_t n_vis, int chunk)
 {
-    const int64_t need_chunks = n_vis / chunk + S + 1;
+    const int64_t need_chunks = dg_schedule_capacity(S, n_vis, chunk, dg_small_items(chunk));
     if (need_chunks > 0x7fffffff)
         return DG_ERR_ARG;
     if (S > p->cap_subgrids) {
@@ -173,7 +173,7 @@ int grid_blocks(degrid_plan *p, int S, int64_t n_vis, int chunk, int max_per_sm,
     if (per_sm > max_per_sm)
         per_sm = max_per_sm;
     int64_t blocks = (int64_t)p->sm_count * per_sm;
-    const int64_t max_chunks = n_vis / chunk + S;
+    const int64_t max_chunks = dg_schedule_capacity(S, n_vis, chunk, dg_small_items(chunk));
     const int64_t useful = (max_chunks + claimers_per_block - 1) / claimers_per_block;
     if (blocks > useful)
         blocks = useful;
@@ -524,8 +524,8 @@ dg_status degrid_execute(degrid_plan_t p, void *stream, int n_subgrids, const vo
     if (st != DG_OK)
         return st;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, p->prefix,
-                                        p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
+    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, dg_small_items(chunk),
+                                        p->prefix, p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);
@@ -574,8 +574,8 @@ dg_status grid_adjoint_execute(degrid_plan_t p, void *stream, int n_subgrids, co
     dg_status st = ensure_capacity(p, n_subgrids, n_vis, chunk);
     if (st != DG_OK)
         return st;
-    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, p->prefix,
-                                        p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
+    cudaError_t e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, chunk, dg_small_items(chunk),
+                                        p->prefix, p->n_chunks, p->chunks, p->cap_chunks, p->work_counter,
                                         p->status);
     if (e != cudaSuccess)
         return from_cuda(e);

@@ -197,12 +197,6 @@ struct Schedule {
     int *work_counter;              // zeroed by the scheduler before every launch
 };
 
-// Launch helpers implemented in schedule.cu.
-cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_subgrids,
-                            int64_t n_vis, int chunk, int *prefix, int *n_chunks,
-                            ChunkDesc *chunks, int capacity, int *work_counter,
-                            DeviceStatus *status);
-
 // Bound on the polls of any device-side wait (mbarrier phase); a wait that
 // exceeds it records kFlagTimeout and the warp stops working.
 constexpr int kSpinLimit = 1 << 22;
@@ -322,6 +316,37 @@ struct NvtxRange {
     NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
+
+namespace dg {
+// A list of fewer than kSparseItems * chunk visibilities is sparse (schedule.cu).
+constexpr int kSparseItems = 64;
+
+// The chunk table of a call (schedule.cu): items of `chunk` visibilities,
+// or with `small` > 0 sparse lists first in items of `small` (capacity from
+// dg_schedule_capacity).
+cudaError_t launch_schedule(cudaStream_t st, const int64_t *vis_offsets, int n_subgrids,
+                            int64_t n_vis, int chunk, int small, int *prefix, int *n_chunks,
+                            ChunkDesc *chunks, int capacity, int *work_counter,
+                            DeviceStatus *status);
+}  // namespace dg
+
+// Items per call that the chunk table must hold: lists are cut into items
+// of `chunk`, sparse lists (fewer than kSparseItems * chunk visibilities)
+// into items of `small` (if > 0), each list ending in one partial item.
+inline int64_t dg_schedule_capacity(int S, int64_t n_vis, int chunk, int small)
+{
+    int64_t need = n_vis / chunk + S + 1;
+    if (small > 0) {
+        const int64_t sparse = n_vis / small + S;
+        const int64_t bound = (int64_t)S * (dg::kSparseItems * (int64_t)chunk / small + 1);
+        need += sparse < bound ? sparse : bound;
+    }
+    return need;
+}
+
+// Item size of the sparse lists in the allocating entry points (0: the
+// fixed-scratch entry point keeps one item size).
+inline int dg_small_items(int chunk) { return chunk > 64 ? 64 : 0; }
 
 // Kernel launchers (one per translation unit).
 cudaError_t dg_launch_degrid(degrid_plan *p, cudaStream_t st, const void *subgrids,

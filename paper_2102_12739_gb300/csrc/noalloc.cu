@@ -152,7 +152,7 @@ extern "C" dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz
     cudaError_t e = cudaMemsetAsync(p.status, 0, sizeof(dg::DeviceStatus), s);
     if (e != cudaSuccess || n_vis == 0)
         return from_cuda(e);
-    e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, p.chunk, p.prefix, p.n_chunks,
+    e = dg::launch_schedule(s, vis_offsets, n_subgrids, n_vis, p.chunk, 0, p.prefix, p.n_chunks,
                             p.chunks, p.cap_chunks, p.work_counter, p.status);
     if (e != cudaSuccess)
         return from_cuda(e);
