@@ -133,7 +133,12 @@ void degrid_plan_destroy(degrid_plan_t plan);
  * tunes N_b, the visibilities per thread block, by hand; Section "Results").
  *   chunk            visibilities per work item claimed by one warp
  *                    (multiple of 32, 32 .. 65536); a work item never
- *                    straddles two subgrids.  Every item is one atomic
+ *                    straddles two subgrids.  Lists of fewer than
+ *                    64 * chunk visibilities (sparse: few visibilities
+ *                    share a footprint) are cut into items of 64 instead
+ *                    and claimed before the others, so that no costly
+ *                    item is left for the end of a call (chunk > 64;
+ *                    results do not depend on it).  Every item is one atomic
  *                    claim on a single device-wide counter: items of
  *                    fewer than 64 visibilities (one pipeline step) make
  *                    every step a claim and the counter then bounds the

@@ -2,20 +2,22 @@
 //
 // The paper launches a grid of max_S(N_vis,S / N_b) x S thread blocks
 // (Eq. 1) and notes that uneven visibility counts leave most of it idle.
-// Here the visibilities of every subgrid are cut into chunks of `chunk`
-// visibilities (a chunk never straddles two subgrids), the chunks of all
-// subgrids are numbered consecutively, and a persistent grid claims them
-// with an atomic counter, so the load is balanced whatever the counts are.
+// Here the visibilities of every subgrid are cut into work items (an item
+// never straddles two subgrids): sparse lists into items of `small`
+// visibilities at the front of the table, the others into items of
+// `chunk` after them (list_items below).  A persistent grid claims the items
+// in table order with an atomic counter, so the load is balanced whatever
+// the counts are, and the expensive sparse items are done first.
 //
 // The chunk table is built on the device, so no host synchronisation is
 // needed and the whole call can be captured in a CUDA graph.  For up to
-// kSchedMaxS subgrids one kernel does it: every block scans
-// ceil(count_s / chunk) over all subgrids into its shared memory (the scan
-// is small and every block gets the same result), block 0 also validates
-// vis_offsets and resets the work counter, and each block writes the chunk
-// descriptors (s, count, first visibility) of its share of the subgrids.
-// Larger stacks take two kernels: chunk_prefix (one block scans into
-// prefix[S + 1] in global memory) and chunk_fill (the descriptors).
+// kSchedMaxS subgrids one kernel does it: every block scans the item counts
+// of all subgrids into the starts in its shared memory (the scan is small
+// and every block gets the same result), block 0 also validates vis_offsets
+// and resets the work counter, and each block writes the descriptors
+// (s, count, first visibility) of its share of the subgrids.  Larger stacks
+// take two kernels: chunk_prefix (one block scans into prefix[S + 1] in
+// global memory) and chunk_fill (the descriptors).
 #include "internal.cuh"
 
 namespace dg {
