@@ -110,8 +110,10 @@ __device__ long long scan_chunks(const int64_t *__restrict__ offs, int S, int64_
         if (lead && (offs[0] != 0 || offs[S] != n_vis))
             atomicOr(&status->flags, kFlagOffsets);
     }
-    // one pass over the lists: the items of the sparse ones and of the dense
-    // ones before each list (the sparse part ends where the dense one starts)
+    // pass 0 (only with small > 0) totals the sparse lists' items; pass 1
+    // scans the (sparse, dense) item counts and writes each list's start: a
+    // sparse list after the sparse items before it, a dense one after all
+    // sparse items and the dense items before it
     long long sp_total = 0;
     for (int pass = small > 0 ? 0 : 1; pass < 2; ++pass) {
         __syncthreads();
