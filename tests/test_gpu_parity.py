@@ -687,22 +687,30 @@ def test_many_subgrids_take_the_two_kernel_schedule():
     # more than 4096 subgrids: the scan and the chunk table are two kernels
     # (one block scans all counts) instead of one; small 16 x 16 x 4 subgrids,
     # ragged and empty lists, element by element against the oracle
+    # (at chunk 128 the tiny lists form a sparse class claimed first and the
+    # long ones stay dense; the long lists keep the call from halving its
+    # chunk, as calls too small for two items per warp do)
     d = dev()
     shape = (16, 16, 4)
     rng = np.random.default_rng(71)
     counts = rng.integers(0, 24, 5000)
     counts[[0, 17, 4999]] = 0
+    counts[[5, 2500, 4998]] = [400000, 300000, 17000]
     w = small_workload(list(counts), kind="scatter", shape=shape, seed=71)
     sub_np = synth.subgrid_stack(len(counts), shape=shape)
     sub, uvw, offs = upload(w, sub_np)
+    ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
+    assert bad == 0
+    outs = []
     with dg.DegridPlan(shape=shape, device=d) as p:
-        for chunk in (32, 64):
+        for chunk in (32, 64, 128):
             p.set_tuning(chunk, 8, 0)
             got = p.degrid(sub, uvw, offs).cpu().numpy()
             assert p.status() == 0
-            ref, bad = oracle.degrid(G_UV, G_W, sub_np.astype(np.complex128), w.uvw, w.vis_offsets)
-            assert bad == 0
             assert rel_l2(got, ref) <= TOL["c64"]
+            outs.append(got)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o.view(np.uint64), outs[0].view(np.uint64))
 
 
 @pytest.mark.parametrize("nz", [5, 8])
@@ -816,3 +824,42 @@ def test_plans_of_different_sizes_from_several_host_threads():
     for res in outs.values():
         for r in res:
             assert torch.equal(torch.view_as_real(r).view(torch.int32), torch.view_as_real(ref).view(torch.int32))
+
+
+def test_sparse_and_dense_lists_at_every_chunk_size():
+    # lists on both sides of each chunk size's sparse threshold (64 x chunk
+    # visibilities: the sparse ones are cut into items of 64 and claimed
+    # first), so every chunk size classes them differently; two long lists
+    # keep the call large enough that no chunk size is halved.  The same bits
+    # come out every time, and they match the oracle (sampled; the gridding
+    # over the whole stack)
+    d = dev()
+    counts = [100, 1_500_000, 20000, 5000, 40000, 0, 300, 16383, 16384, 8191, 8192, 1, 1_000_000]
+    w = small_workload(counts, kind="mixed", seed=99)
+    sub_np = synth.subgrid_stack(len(counts), seed=100)
+    sub, uvw, offs = upload(w, sub_np)
+    outs = []
+    with dg.DegridPlan(device=d) as p:
+        # chunk 64: one class; 128, 256: thresholds 8192, 16384; 1024 is
+        # halved to 512 for this call (threshold 32768)
+        for chunk, warps in ((64, 8), (128, 4), (256, 8), (1024, 8), (256, 2)):
+            p.set_tuning(chunk, warps, 0)
+            o = p.degrid(sub, uvw, offs).cpu().numpy()
+            assert p.status() == 0
+            outs.append(o)
+        p.set_tuning(256, 8, 0)
+        yv = synth.adjoint_vis(w.n_vis, seed=101)
+        g = p.grid(torch.from_numpy(yv).to(d), uvw, offs, len(counts)).cpu().numpy()
+        assert p.status() == 0
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o.view(np.uint64), outs[0].view(np.uint64))
+    rng = np.random.default_rng(102)
+    picks = []
+    for s_ in range(len(counts)):
+        lo, hi = w.vis_offsets[s_], w.vis_offsets[s_ + 1]
+        if hi > lo:
+            picks += [lo, hi - 1] + list(rng.integers(lo, hi, 300))
+    idx, ref = oracle_degrid_sample(w, lambda s_: sub_np[s_], np.unique(picks))
+    assert rel_l2(outs[0][idx], ref) <= TOL["c64"]
+    gref, _ = oracle.grid(G_UV, G_W, synth.SUBGRID_SHAPE, len(counts), w.uvw, w.vis_offsets, yv)
+    assert rel_l2(g, gref) <= TOL["c64"]
