@@ -70,13 +70,15 @@ def _store_cache(cache: dict) -> None:
 
 
 def cache_key(plan, n_subgrids: int, n_vis: int) -> str:
-    """GPU, storage type, subgrid shape and the orders of magnitude of S and N."""
+    """GPU, storage type, G_uv table kind, reduction, subgrid shape and the
+    orders of magnitude of S and N."""
     import torch
     name = torch.cuda.get_device_name(plan.device)
     ny, nx, nz = plan.shape
-    return "%s|%s|%dx%dx%d|S~2^%d|N~2^%d" % (
-        name, plan.dtype, ny, nx, nz, int(math.log2(max(n_subgrids, 1))),
-        int(math.log2(max(n_vis, 1))))
+    return "%s|%s|%s|%s|%dx%dx%d|S~2^%d|N~2^%d" % (
+        name, plan.dtype, "2d" if getattr(plan, "table2d", False) else "sep",
+        "comp" if plan.compensated else "plain", ny, nx, nz,
+        int(math.log2(max(n_subgrids, 1))), int(math.log2(max(n_vis, 1))))
 
 
 def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
@@ -94,8 +96,11 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
     key = cache_key(plan, S, n)
     cache = _load_cache() if use_cache else {}
     if key in cache:
-        _apply(plan, cache[key]["tuning"])
-        return dict(cache[key], tuning=plan.tuning(), cached=True)
+        try:
+            _apply(plan, cache[key]["tuning"])
+            return dict(cache[key], tuning=plan.tuning(), cached=True)
+        except Exception:
+            pass            # a tuning this plan cannot take (an old or foreign entry): time again
     if os.environ.get("DEGRID_TUNE", "1") == "0":
         return {"tuning": plan.tuning(), "ms": None, "timings": [], "cached": False}
     cands = list(candidates) if candidates is not None else list(DEFAULT_CANDIDATES)
