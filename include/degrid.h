@@ -138,9 +138,11 @@ void degrid_plan_destroy(degrid_plan_t plan);
  *                    share a footprint) are cut into items of 64 instead
  *                    and claimed before the others, so that no costly
  *                    item is left for the end of a call (chunk > 64;
- *                    results do not depend on it).  Every item is one atomic
- *                    claim on a single device-wide counter: items of
- *                    fewer than 64 visibilities (one pipeline step) make
+ *                    results do not depend on it).  A call too small for
+ *                    two items per resident warp halves its chunk, down to
+ *                    64, so that it still spreads over the GPU.  Every item
+ *                    is one atomic claim on a single device-wide counter:
+ *                    items of fewer than 64 visibilities (one pipeline step) make
  *                    every step a claim and the counter then bounds the
  *                    call (gridding measured 18x slower at 32 than at
  *                    256); 128 .. 1024 is the useful range, the one the
