@@ -83,6 +83,28 @@ const char *degrid_status_string(dg_status status);
 const char *degrid_version(void);
 
 /*
+ * Scratch sizing of a plan (host arithmetic only, no GPU needed).  The
+ * paper's launch (Eq. 1) needs no scratch; the persistent scheduler here
+ * keeps a table of 16-byte work items per plan.  For a GPU with `sm_count`
+ * SMs and a plan whose tuned chunk is `plan_chunk` (degrid_plan_set_tuning),
+ * a call with n_subgrids subgrids and n_vis visibilities
+ *   call_chunk_out  (may be NULL) cuts dense lists into items of this many
+ *                   visibilities: plan_chunk, halved (down to 64) while the
+ *                   call would give fewer than two items to each of the
+ *                   16 * sm_count resident warps;
+ *   items_out       (may be NULL) makes the plan reserve this many items
+ *                   (16 bytes each): enough for the call itself and for
+ *                   every call with at most n_subgrids subgrids and n_vis
+ *                   visibilities, whatever chunk those get.  The reserve
+ *                   never decreases as n_subgrids or n_vis grow, so after a
+ *                   call with the largest sizes no smaller call allocates.
+ * Returns DG_ERR_ARG for sm_count < 1, a plan_chunk that is not a multiple
+ * of 32 in [32, 65536], or negative sizes.
+ */
+dg_status degrid_schedule_reserve(int sm_count, int plan_chunk, int n_subgrids, int64_t n_vis,
+                                  int *call_chunk_out, int64_t *items_out);
+
+/*
  * Create a plan (Section "Implementation": the precomputed oversampled GCFs
  * and the 512 x 512 x 4 subgrid shape are the fixed inputs of the method).
  *   out            receives the plan handle (set to NULL on failure)
@@ -290,8 +312,10 @@ dg_status degrid_measure_l2_read_bw(int device, double *gbs);
  * Accumulation is FP32; the coordinate step is exact integer arithmetic on
  * the FP64 coordinates.  Malformed vis_offsets are flagged for
  * degrid_get_status; subgrids with a negative count are skipped.
- * The plan's scratch grows on the first call with a larger S or N; call once
- * with the largest sizes before capturing the call in a CUDA graph.
+ * The plan's scratch grows on the first call with a larger S or N (see
+ * degrid_schedule_reserve: what a call reserves covers every call with
+ * smaller S and N); call once with the largest sizes before capturing calls
+ * in a CUDA graph.
  */
 dg_status degrid_execute(degrid_plan_t plan, void *stream, int n_subgrids,
                          const void *subgrids, const float *subgrid_scale,

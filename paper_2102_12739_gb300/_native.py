@@ -40,6 +40,7 @@ _I64 = ctypes.c_int64
 SIGNATURES = {
     "degrid_status_string": (ctypes.c_char_p, [_I]),
     "degrid_version": (ctypes.c_char_p, []),
+    "degrid_schedule_reserve": (_I, [_I, _I, _I, _I64, ctypes.POINTER(_I), ctypes.POINTER(_I64)]),
     "degrid_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _P, _I, _I, _P, _I, _I, _I, _I]),
     "degrid_plan_destroy": (None, [_P]),
     "degrid_plan_set_tuning": (_I, [_P, _I, _I, _I]),

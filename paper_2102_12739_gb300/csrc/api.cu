@@ -89,26 +89,55 @@ void free_plan_buffers(degrid_plan *p)
     cudaFree(p->chunks);
 }
 
+// Resident warps a call's chunk size is matched to (16 per SM).
+constexpr int kCallWarpsPerSm = 16;
+
 // Chunk size of one call: the plan's, halved for small calls until the
 // list makes about two chunks per resident warp (so that a short list still
 // spreads over the GPU), but never below one 64-visibility pipeline step.
 // Results do not depend on it (every visibility's arithmetic is the same).
-int call_chunk(const degrid_plan *p, int64_t n_vis)
+int call_chunk_for(int sm_count, int plan_chunk, int64_t n_vis)
 {
-    const int64_t warps = (int64_t)p->sm_count * 16;
-    int c = p->chunk;
+    const int64_t warps = (int64_t)sm_count * kCallWarpsPerSm;
+    int c = plan_chunk;
     while (c > 64 && c % 64 == 0 && n_vis / c < 2 * warps)
         c >>= 1;
     return c;
 }
 
-// Grows the schedule scratch so that S subgrids and n_vis visibilities fit
-// in chunks of `chunk`.  This allocates, so it must not run inside a stream
-// capture: the first call with the largest sizes has to happen before
-// capturing.
+int call_chunk(const degrid_plan *p, int64_t n_vis) { return call_chunk_for(p->sm_count, p->chunk, n_vis); }
+
+// Work items the chunk table reserves for calls of up to S subgrids and
+// n_vis visibilities: the most that any such call needs, whatever chunk
+// call_chunk_for picks for it.  A chunk c below the plan's is picked only
+// when the halving test held at 2c, i.e. for n < 4 * warps * c visibilities,
+// so the items of that chunk are bounded at min(n_vis, 4 * warps * c - 1).
+// Each term grows with S and n_vis, so the reserve does too: a call never
+// needs more items than one with larger sizes reserved before it (so a call
+// captured in a CUDA graph after a call with larger sizes never allocates).
+int64_t reserve_items(int sm_count, int plan_chunk, int S, int64_t n_vis)
+{
+    int64_t need = dg_schedule_capacity(S, n_vis, plan_chunk, dg_small_items(plan_chunk));
+    const int64_t warps = (int64_t)sm_count * kCallWarpsPerSm;
+    for (int c = plan_chunk; c > 64 && c % 64 == 0;) {
+        c >>= 1;
+        const int64_t bound = 4 * warps * c - 1;
+        const int64_t n = n_vis < bound ? n_vis : bound;
+        const int64_t k = dg_schedule_capacity(S, n, c, dg_small_items(c));
+        if (k > need)
+            need = k;
+    }
+    return need;
+}
+
+// Grows the schedule scratch so that every call of up to S subgrids and
+// n_vis visibilities fits (reserve_items).  This allocates, so it must not
+// run inside a stream capture: a first call with sizes at least as large
+// has to happen before capturing.
 dg_status ensure_capacity(degrid_plan *p, int S, int64_t n_vis, int chunk)
 {
-    const int64_t need_chunks = dg_schedule_capacity(S, n_vis, chunk, dg_small_items(chunk));
+    (void)chunk;
+    const int64_t need_chunks = reserve_items(p->sm_count, p->chunk, S, n_vis);
     if (need_chunks > 0x7fffffff)
         return DG_ERR_ARG;
     if (S > p->cap_subgrids) {
@@ -202,6 +231,19 @@ const char *degrid_status_string(dg_status status)
 }
 
 const char *degrid_version(void) { return "gb300-degrid 0.1 (sm_103a)"; }
+
+dg_status degrid_schedule_reserve(int sm_count, int plan_chunk, int n_subgrids, int64_t n_vis,
+                                  int *call_chunk_out, int64_t *items_out)
+{
+    if (sm_count < 1 || plan_chunk < dg::kWarp || plan_chunk % dg::kWarp != 0 || plan_chunk > 65536 ||
+        n_subgrids < 0 || n_vis < 0)
+        return DG_ERR_ARG;
+    if (call_chunk_out)
+        *call_chunk_out = call_chunk_for(sm_count, plan_chunk, n_vis);
+    if (items_out)
+        *items_out = reserve_items(sm_count, plan_chunk, n_subgrids, n_vis);
+    return DG_OK;
+}
 
 // Plan creation for either a separable G_uv table g_uv [O][8] or a 2D one
 // g_uv2 [O][O][8][8] (exactly one of them non-null).

@@ -96,14 +96,18 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
     key = cache_key(plan, S, n)
     cache = _load_cache() if use_cache else {}
     if key in cache:
+        before = plan.tuning()
         try:
             _apply(plan, cache[key]["tuning"])
             return dict(cache[key], tuning=plan.tuning(), cached=True)
         except Exception:
-            pass            # a tuning this plan cannot take (an old or foreign entry): time again
+            # a tuning this plan cannot take (an old or foreign entry): the
+            # part of it already applied is undone, then it is timed again
+            _apply(plan, before)
     if os.environ.get("DEGRID_TUNE", "1") == "0":
         return {"tuning": plan.tuning(), "ms": None, "timings": [], "cached": False}
     cands = list(candidates) if candidates is not None else list(DEFAULT_CANDIDATES)
+    before_timing = plan.tuning()
     out = torch.empty(n, dtype=torch.complex64, device=plan.device)
     plan.enable_timing(max(iters, 1))
     timings = []
@@ -116,6 +120,7 @@ def autotune(plan, subgrids, uvw, vis_offsets, scale=None,
                 _apply(plan, {"chunk": chunk, "warps_per_block": warps, "blocks_per_sm": bps,
                               "direct_runs": direct, "gather": gather})
             except Exception:
+                _apply(plan, before_timing)
                 continue
             for _ in range(2):                      # warm-up (also sizes scratch)
                 plan.degrid(subgrids, uvw, vis_offsets, scale=scale, out=out)

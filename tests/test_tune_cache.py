@@ -84,3 +84,17 @@ def test_a_corrupted_cache_file_reads_as_empty(cache_file):
     r = call(plan)
     assert not r["cached"] and r["tuning"]["chunk"] == 128
     assert json.loads(cache_file.read_text())["key"]["tuning"]["chunk"] == 128
+
+
+def test_a_refused_cached_tuning_leaves_the_plan_as_it_was(cache_file, monkeypatch):
+    # with timing disabled the autotuner returns the plan's own tuning: no
+    # part of the refused entry (its chunk, warps or direct-arm threshold)
+    # may stay applied
+    monkeypatch.setenv("DEGRID_TUNE", "0")
+    cache_file.write_text(json.dumps({"key": {"tuning": {"chunk": 1024, "warps_per_block": 4, "blocks_per_sm": 3,
+                                                         "direct_runs": 9, "gather": 1}, "ms": 0.1}}))
+    plan = FakePlan()
+    before = plan.tuning()
+    r = call(plan)
+    assert not r["cached"] and plan.timed == 0
+    assert plan.tuning() == before and r["tuning"] == before
