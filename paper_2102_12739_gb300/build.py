@@ -88,7 +88,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 # GCF rows, 2D weight block, copy-engine box) against the buffers' extents
 # and reports a violation through degrid_get_status (DG_ERR_BOUNDS) instead
 # of touching memory; the index-safety check the GPU tests run against.
-VARIANTS = {"bounds": ("DEGRID_BOUNDS_CHECK",)}
+# "timeout" gives the gather kernel's wait for a stage a limit of zero polls
+# from a warp's fourth stage on (its copies are then still in flight), so
+# that the bounded-wait path runs: the flag that degrid_get_status reports
+# as DG_ERR_TIMEOUT, and the full-bound wait for the copies in flight before
+# the warp ends; each warp's first three stages are summed normally.
+VARIANTS = {"bounds": ("DEGRID_BOUNDS_CHECK",),
+            "timeout": ("DG_GATHER_SUM_WAIT_FROM=3", "DG_GATHER_SUM_WAIT_POLLS=0")}
 
 
 def variant_path(name: str) -> str:

@@ -58,6 +58,24 @@ namespace {
 constexpr int kGVis = 4;            // visibilities per stage (8 lanes each)
 constexpr int kGStages = DG_GATHER_STAGES;
 
+// Polls of a warp's wait for a stage before it sums it.  The product build
+// waits up to kSpinLimit polls for every stage.  The library variant that
+// tests the timeout path waits normally for a warp's first
+// DG_GATHER_SUM_WAIT_FROM stages and then with a limit of
+// DG_GATHER_SUM_WAIT_POLLS (0: the wait gives up at once, while the stage's
+// copies are in flight), so every warp that gets that far records the
+// timeout and stops.  The wait for the copies still in flight after a
+// timeout always keeps the full bound, so every copy a warp issued has
+// landed before the warp ends.
+#ifndef DG_GATHER_SUM_WAIT_POLLS
+#define DG_GATHER_SUM_WAIT_POLLS kSpinLimit
+#endif
+#ifndef DG_GATHER_SUM_WAIT_FROM
+#define DG_GATHER_SUM_WAIT_FROM 0
+#endif
+constexpr int kSumWaitPolls = DG_GATHER_SUM_WAIT_POLLS;
+constexpr int kSumWaitFrom = DG_GATHER_SUM_WAIT_FROM;
+
 template <int DT>
 struct GatherShape {
     static constexpr int kPitch = FootprintBox<DT>::kPitch;              // box row in shared memory
@@ -298,7 +316,8 @@ degrid_gather_kernel(const Geometry g, const __grid_constant__ CUtensorMap tmap,
                                   status, lane);
         GatherSlot<DT> &sl = slots[done % kGStages];
         cp_async_wait<kGStages - 1>();                  // this lane's row copies of stage `done`
-        if (!mbar_wait_bounded(smem_u32(&sl.bar), (unsigned)(done / kGStages) & 1u)) {
+        if (!mbar_wait_bounded(smem_u32(&sl.bar), (unsigned)(done / kGStages) & 1u,
+                               done < kSumWaitFrom ? kSpinLimit : kSumWaitPolls)) {
             if (lane == 0)
                 atomicOr(&status->flags, kFlagTimeout);
             break;
@@ -307,9 +326,10 @@ degrid_gather_kernel(const Geometry g, const __grid_constant__ CUtensorMap tmap,
         sum_stage<DT, COMP>(sl, wtab, gwt, scale, vis_out, lane);
         __syncwarp();
     }
-    // after a timeout: wait (bounded) for the copies still in flight
+    // after a timeout: wait (bounded, the full kSpinLimit) for the copies
+    // still in flight
     for (; done < issued; ++done)
-        mbar_wait_bounded(smem_u32(&slots[done % kGStages].bar), (unsigned)(done / kGStages) & 1u);
+        mbar_wait_bounded(smem_u32(&slots[done % kGStages].bar), (unsigned)(done / kGStages) & 1u, kSpinLimit);
     cp_async_wait<0>();
 }
 

@@ -52,12 +52,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity)
     return ok != 0;
 }
 
-// Waits for phase `parity` of the mbarrier, polling at most kSpinLimit
-// times; returns false (on every lane) when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity)
+// Waits for phase `parity` of the mbarrier, polling at most `limit` times;
+// returns false (on every lane) when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity, int limit = kSpinLimit)
 {
     bool ok = false;
-    for (int i = 0; i < kSpinLimit && !ok; ++i)
+    for (int i = 0; i < limit && !ok; ++i)
         ok = mbar_try_wait(bar, parity);
     return __all_sync(kFull, ok);
 }
