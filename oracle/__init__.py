@@ -8,7 +8,9 @@ The arithmetic lives in ``oracle.c`` (plain double-precision loops, see its
 header for the readings of the paper it encodes); this module compiles it
 with gcc on first use and wraps it with ctypes.  It also holds the reference
 for the per-subgrid FP16/BF16 storage format (``quantize``), written with
-numpy from the IEEE-754 definitions.
+numpy from the IEEE-754 definitions.  ``oracle.predict`` (numpy, FP64) is
+the reference of the step upstream of degridding that produces the subgrid
+stack (the w-plane grids of improved w-stacking).
 """
 from __future__ import annotations
 

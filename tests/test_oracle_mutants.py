@@ -51,3 +51,50 @@ def test_pins_kill_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# ---- the subgrid producer's oracle (oracle/predict.py) ----------------------
+
+PREDICT_SRC = os.path.join(ROOT, "oracle", "predict.py")
+
+PREDICT_MUTANTS = {
+    "w_phase_sign": ("np.exp(-2j * np.pi * (turns_uv + w * nm1))", "np.exp(-2j * np.pi * (turns_uv - w * nm1))"),
+    "l_m_swapped": ("turns_uv = ((u0 * a[None, :] + v0 * a[:, None]) % N)",
+                    "turns_uv = ((u0 * a[:, None] + v0 * a[None, :]) % N)"),
+    "shift_order": ("np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(J)))", "np.fft.fftshift(np.fft.fft2(J))"),
+    "inverse_transform": ("np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(J)))",
+                          "np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(J))) * N * N"),
+    "plane_spacing": ("J = img * T * _screen(N, theta, int(u0), int(v0), w0 + c * dw)",
+                      "J = img * T * _screen(N, theta, int(u0), int(v0), w0 + c * dw * 0.5)"),
+    "taper_dropped": ("J = img * T * _screen(", "J = img * _screen("),
+    "pixel_centre_off_by_one": ("idx = (np.arange(N, dtype=np.float64) - N // 2) * (theta / N)",
+                                "idx = (np.arange(N, dtype=np.float64) - N // 2 + 1) * (theta / N)"),
+}
+
+
+@pytest.mark.parametrize("name", ["unchanged"] + sorted(PREDICT_MUTANTS))
+def test_predict_pins_kill_mutant(name, tmp_path):
+    # "unchanged" runs the harness on the oracle as it is: the pins pass
+    before, after = PREDICT_MUTANTS.get(name, ("", ""))
+    src = open(PREDICT_SRC).read()
+    assert before in src, "mutation site not found: update the mutant"
+    pkg = tmp_path / "mutpkg" / "oracle"
+    pkg.mkdir(parents=True)
+    (pkg / "__init__.py").write_text("")
+    (pkg / "predict.py").write_text(src.replace(before, after, 1))
+    # the pins run from a copy beside the mutated package, so that `oracle`
+    # resolves to the mutant and not to the repository's package
+    test = tmp_path / "mutpkg" / "test_pins.py"
+    test.write_text(open(os.path.join(ROOT, "tests", "test_oracle_predict.py")).read())
+    env = dict(os.environ, PYTHONPATH=str(tmp_path / "mutpkg"))
+    probe = subprocess.run([sys.executable, "-c", "import oracle.predict as m; print(m.__file__)"],
+                           cwd=str(tmp_path / "mutpkg"), env=env, capture_output=True, text=True)
+    assert probe.stdout.strip() == str(pkg / "predict.py"), probe.stdout + probe.stderr
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "--rootdir",
+                        str(tmp_path / "mutpkg"), "-c", os.devnull, str(test)],
+                       cwd=str(tmp_path / "mutpkg"), env=env, capture_output=True, text=True, timeout=600)
+    assert "ModuleNotFoundError" not in r.stdout + r.stderr, r.stdout[-2000:]
+    if name == "unchanged":
+        assert r.returncode == 0, r.stdout[-2000:]
+    else:
+        assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
