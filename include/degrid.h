@@ -293,6 +293,17 @@ dg_status degrid_measure_fp32_peak(int device, int packed, double *tflops);
 dg_status degrid_measure_l2_read_bw(int device, double *gbs);
 
 /*
+ * The rate, in GB/s of added data, at which the copy engines apply tensor
+ * reduce-adds of 2 KB footprint tiles (8 rows x 256 bytes of FP32 pairs at
+ * footprint positions) into an L2-resident stack, one stream of them per
+ * warp of a CTA of 16 warps on every SM: the bound of the gridding kernel
+ * for scattered coverage (no counterpart in the paper).  Synchronous; makes
+ * `device` current for the call.  Returns DG_OK, DG_ERR_ARG, DG_ERR_OOM or
+ * DG_ERR_CUDA.
+ */
+dg_status degrid_measure_l2_reduce_bw(int device, double *gbs);
+
+/*
  * Degridding (Section "Implementation", the weighted footprint sum):
  *   vis_out[i] = sum_{b<8} sum_{a<8} sum_{c<4} g_uv[fv][b] g_uv[fu][a]
  *                g_w[fw][c] * sub[s][y0+b][x0+a][z0+c]
@@ -461,6 +472,54 @@ dg_status degrid_execute_noalloc(void *stream, int nx, int ny, int nz,
                                  const float *subgrid_scale, const double *uvw,
                                  const int64_t *vis_offsets, int64_t n_vis,
                                  float *vis_out, unsigned long long *status_out);
+
+/*
+ * The subgrid stack itself: the step upstream of degridding.  The paper
+ * takes the stack as "pre-computed grid data" of the improved w-stacking
+ * method (Introduction) and does not describe it; following improved
+ * w-stacking (Ye, Gull, Tan & Nikolic 2020), the grid at a w-plane is the
+ * Fourier transform of the corrected sky image times the plane's w-phase
+ * screen.  For an N x N image I (row b <-> m, column a <-> l, direction
+ * cosines l_a = (a - N/2) theta / N, m_b likewise) and a real image-plane
+ * correction T, subgrid s is
+ *   G[s][y][x][c] = sum_{b,a} I[b][a] T[b][a]
+ *       exp(-2 pi i ((x - N/2 + u0_s)(a - N/2) / N + (y - N/2 + v0_s)(b - N/2) / N
+ *                     + (w0_s + c dw_s)(n_ab - 1))),   n_ab = sqrt(1 - l_a^2 - m_b^2),
+ * for cells x, y < N and w-planes c < nz (pixels with l^2 + m^2 >= 1 add
+ * nothing): the uv cells (x - N/2 + u0_s, y - N/2 + v0_s) / theta
+ * wavelengths at w = w0_s + c dw_s, laid out [S][N][N][nz] as degrid_execute
+ * reads them (DG_C64).
+ *
+ * subgrid_predict_plan_create
+ *   n                  image and subgrid side N: even, >= 8, N * N * nz < 2^31
+ *   nz                 w-planes per subgrid, 1 .. 64 (4 for the paper's stack)
+ *   subgrids_per_pass  subgrids transformed together (1 .. 4096); the plan
+ *                      holds a work buffer of subgrids_per_pass * nz * N * N
+ *                      complex64 and a batched 2D FFT plan (cuFFT)
+ *   device             CUDA device ordinal
+ * Returns DG_OK, DG_ERR_ARG, DG_ERR_OOM or DG_ERR_CUDA.
+ *
+ * subgrid_predict_execute (asynchronous on `stream`; no allocation)
+ *   theta         image width in direction cosines (> 0, finite)
+ *   image         DEVICE complex64 [N][N], 8-byte aligned
+ *   taper         DEVICE float [N][N] (the gridding correction T), or NULL for 1
+ *   n_subgrids    S >= 0
+ *   uv_offsets    DEVICE int32 [S][2]: (u0_s, v0_s) integer cell offsets
+ *   w_planes      DEVICE double [S][2]: (w0_s, dw_s) in wavelengths
+ *   subgrids_out  DEVICE complex64 [S][N][N][nz], every element written
+ * Returns DG_OK, DG_ERR_ARG (NULL or misaligned pointers, bad theta) or
+ * DG_ERR_CUDA.  Arithmetic: FP32; the w-phase w (n - 1) is reduced to a
+ * fraction of a turn in double-float arithmetic (exact to about 3e-8 turns
+ * while |w (n - 1)| < 2^22 turns) before its sine and cosine.
+ */
+typedef struct subgrid_predict_plan *subgrid_predict_plan_t;
+dg_status subgrid_predict_plan_create(subgrid_predict_plan_t *out, int n, int nz, int subgrids_per_pass,
+                                      int device);
+dg_status subgrid_predict_execute(subgrid_predict_plan_t plan, void *stream, double theta,
+                                  const float *image, const float *taper, int n_subgrids,
+                                  const int32_t *uv_offsets, const double *w_planes,
+                                  float *subgrids_out);
+void subgrid_predict_plan_destroy(subgrid_predict_plan_t plan);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,8 @@ Main objects:
   pack_subgrids     complex64 -> FP16/BF16 storage with per-subgrid scale
   DegridFn          torch.autograd.Function, backward = adjoint kernel
   autotune          pick chunk / warps / blocks per SM by timing
+  SubgridPredictor  the subgrid stack from a sky image (the w-plane grids of
+                    improved w-stacking, upstream of degridding)
 """
 from __future__ import annotations
 
@@ -26,7 +28,8 @@ from ._native import (DG_C32_BF16, DG_C32_F16, DG_C64, DG_ERR_OFFSETS, DG_OK,  #
                       DegridError, SIGNATURES, check, lib_path, load, status_string)
 
 __all__ = ["DegridPlan", "DegridFn", "DegridError", "pack_subgrids", "degrid", "autotune",
-           "measure_fp32_peak", "measure_l2_read_bw", "synth", "load", "lib_path", "SIGNATURES"]
+           "measure_fp32_peak", "measure_l2_read_bw", "measure_l2_reduce_bw", "synth", "load", "lib_path", "SIGNATURES",
+           "SubgridPredictor"]
 
 DTYPES = {"c64": DG_C64, "f16": DG_C32_F16, "bf16": DG_C32_BF16}
 
@@ -402,6 +405,15 @@ def measure_l2_read_bw(device: int = 0) -> float:
     return float(out.value)
 
 
+def measure_l2_reduce_bw(device: int = 0) -> float:
+    """Rate of tensor reduce-adds of 2 KB footprint tiles into an L2-resident
+    stack, GB/s of added data (degrid_measure_l2_reduce_bw)."""
+    out = ctypes.c_double(0.0)
+    check(load().degrid_measure_l2_reduce_bw(int(device), ctypes.byref(out)),
+          "degrid_measure_l2_reduce_bw")
+    return float(out.value)
+
+
 def degrid(plan: DegridPlan, subgrids, uvw, vis_offsets, scale=None):
     """Functional form of DegridPlan.degrid."""
     return plan.degrid(subgrids, uvw, vis_offsets, scale=scale)
@@ -451,3 +463,73 @@ def autotune(plan: DegridPlan, subgrids, uvw, vis_offsets, scale=None, **kw):
     """Time tuning candidates on the given inputs and keep the fastest."""
     from .tune import autotune as _autotune
     return _autotune(plan, subgrids, uvw, vis_offsets, scale=scale, **kw)
+
+
+class SubgridPredictor:
+    """The subgrid stack from an N x N sky image (subgrid_predict_execute):
+    for subgrid s the cells (x - N/2 + u0_s, y - N/2 + v0_s) / theta of the
+    w-planes w0_s + c dw_s, c < nz, of the tapered image's w-stacked
+    Fourier transform, complex64 [S, N, N, nz] -- the layout DegridPlan
+    reads.
+
+    n, nz              image / subgrid side and w-planes per subgrid
+    subgrids_per_pass  subgrids transformed together (work buffer size)
+    device             CUDA device
+    """
+
+    def __init__(self, n: int = 512, nz: int = 4, subgrids_per_pass: int = 16, device=None):
+        torch = _torch()
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        device = torch.device(device)
+        if device.type != "cuda":
+            raise ValueError("SubgridPredictor needs a CUDA device")
+        if device.index is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device, self.n, self.nz = device, int(n), int(nz)
+        h = ctypes.c_void_p()
+        check(load().subgrid_predict_plan_create(ctypes.byref(h), self.n, self.nz, int(subgrids_per_pass),
+                                                 device.index), "subgrid_predict_plan_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            load().subgrid_predict_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def predict(self, image, theta: float, uv_offsets, w_planes, taper=None, out=None, stream=None):
+        """image complex64 [N, N]; uv_offsets int32 [S, 2]; w_planes float64
+        [S, 2] (w0, dw); taper float32 [N, N] or None -- all on the device."""
+        torch = _torch()
+        if self._h is None:
+            raise RuntimeError("SubgridPredictor is closed")
+        n = self.n
+        _need(image, "image", torch.complex64, self.device, (n, n))
+        if taper is not None:
+            _need(taper, "taper", torch.float32, self.device, (n, n))
+        _need(uv_offsets, "uv_offsets", torch.int32, self.device)
+        S = uv_offsets.shape[0]
+        if tuple(uv_offsets.shape) != (S, 2):
+            raise ValueError("uv_offsets must be [S, 2] int32")
+        _need(w_planes, "w_planes", torch.float64, self.device, (S, 2))
+        if out is None:
+            out = torch.empty((S, n, n, self.nz), dtype=torch.complex64, device=self.device)
+        else:
+            _need(out, "out", torch.complex64, self.device, (S, n, n, self.nz))
+        st = load().subgrid_predict_execute(self._h, _stream_handle(stream, self.device), float(theta),
+                                            _vp(image), _vp(taper), S, _vp(uv_offsets), _vp(w_planes),
+                                            _vp(out))
+        check(st, "subgrid_predict_execute")
+        return out

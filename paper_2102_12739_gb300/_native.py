@@ -57,6 +57,7 @@ SIGNATURES = {
     "degrid_plan_get_gather": (_I, [_P, ctypes.POINTER(_I)]),
     "degrid_measure_fp32_peak": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_measure_l2_read_bw": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
+    "degrid_measure_l2_reduce_bw": (_I, [_I, ctypes.POINTER(ctypes.c_double)]),
     "degrid_plan_enable_timing": (_I, [_P, _I]),
     "degrid_plan_kernel_times_ms": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I,
                                          ctypes.POINTER(_I)]),
@@ -67,6 +68,9 @@ SIGNATURES = {
     "degrid_get_status": (_I, [_P, _P, ctypes.POINTER(_I64)]),
     "degrid_execute_noalloc": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P, _P, _P, _P,
                                     _I64, _P, _P]),
+    "subgrid_predict_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
+    "subgrid_predict_execute": (_I, [_P, _P, ctypes.c_double, _P, _P, _I, _P, _P, _P]),
+    "subgrid_predict_plan_destroy": (None, [_P]),
 }
 
 _lock = threading.Lock()

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(OUT_DIR, "libdegrid.so")
 
 SOURCES = ["api.cu", "schedule.cu", "degrid.cu", "adjoint.cu", "aux_kernels.cu", "noalloc.cu",
            "host_exec.cu", "peak.cu",
-           "gather.cu", "scatter.cu"]
+           "gather.cu", "scatter.cu", "predict.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "-I", INCLUDE, "-I", CSRC]
@@ -36,6 +36,22 @@ def nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libdegrid.so")
+
+
+def cuda_lib_dir() -> str:
+    """The toolkit's library directory (cuFFT for the subgrid producer)."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    for cand in ("lib64", "lib", os.path.join("targets", "sbsa-linux", "lib"),
+                 os.path.join("targets", "x86_64-linux", "lib")):
+        d = os.path.join(root, cand)
+        if os.path.exists(os.path.join(d, "libcufft.so")):
+            return d
+    raise RuntimeError(f"libcufft.so not found under {root}")
+
+
+def link_flags():
+    d = cuda_lib_dir()
+    return ["-L", d, "-lcufft", "-Xlinker", "-rpath," + d]
 
 
 def _inputs():
@@ -75,7 +91,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if log.strip():
                 sys.stderr.write(log)
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], *link_flags()]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
@@ -124,7 +140,7 @@ def build_variant(name: str, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = path + ".tmp%d" % os.getpid()
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, *link_flags()], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, path)

@@ -9,8 +9,13 @@
 //    own 8 x 8 x 4 footprint (2 KB complex64, 1 KB FP16/BF16) from L2.  A
 //    kernel streams an L2-resident buffer into every SM with L1-bypassing
 //    16-byte loads.
-// The host times both with CUDA events (best of 5 launches after a warm-up).
-#include "internal.cuh"
+//  * L2 reduce-add rate: gridding of scattered coverage adds every
+//    visibility's 2 KB footprint tile into the stack with one tensor
+//    reduce-add of the copy engine (scatter.cu).  A kernel has one lane of
+//    every warp issue such reduce-adds (boxes of 8 rows x 256 bytes at
+//    pseudo-random footprint positions of an L2-resident stack) back to back.
+// The host times them with CUDA events (best of 5 launches after a warm-up).
+#include "tma.cuh"
 
 namespace dg {
 namespace {
@@ -81,6 +86,39 @@ l2_read_kernel(const uint4 *__restrict__ buf, long long n4, int passes, unsigned
         }
     }
     out[t] = acc;
+}
+
+constexpr int kRedWarps = 16;                // warps per CTA, one CTA per SM
+constexpr int kRedCols = 2048;              // floats per row of the stack (a 512 x 4 complex64 row)
+constexpr int kRedBoxW = 64;                // floats per box row: one footprint row (8 x 4 complex64)
+constexpr int kRedBoxH = 8;                 // box rows
+
+// Every warp's lane 0 issues `iters` tensor reduce-adds of its 2 KB tile into
+// the stack at pseudo-random footprint positions (x on a 4-sample boundary,
+// as a footprint's is), keeping up to 4 in flight.
+__global__ void __launch_bounds__(kRedWarps * kWarp, 1)
+l2_reduce_kernel(const __grid_constant__ CUtensorMap map, int rows, int iters)
+{
+    __shared__ __align__(128) float tile[kRedWarps][kRedBoxH][kRedBoxW];
+    for (int i = threadIdx.x; i < kRedWarps * kRedBoxH * kRedBoxW; i += blockDim.x)
+        (&tile[0][0][0])[i] = 1e-30f;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane != 0)
+        return;
+    unsigned h = (blockIdx.x * kRedWarps + w) * 2654435761u + 12345u;
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(&tile[w][0][0]);
+    for (int i = 0; i < iters; ++i) {
+        h = h * 1664525u + 1013904223u;
+        const int x = (int)((h >> 8) % (unsigned)(kRedCols / 8 - kRedBoxW / 8 + 1)) * 8;
+        const int y = (int)((h >> 3) % (unsigned)(rows - kRedBoxH + 1));
+        asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group"
+                     " [%0, {%1, %2}], [%3];" ::"l"(&map), "r"(x), "r"(y), "r"(src) : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Times `launch` (a callable issuing one launch on `st`): best of 5 after a
@@ -199,5 +237,44 @@ extern "C" dg_status degrid_measure_l2_read_bw(int device, double *gbs)
     if (e != cudaSuccess || best <= 0.0f)
         return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
     *gbs = (double)passes * (double)n4 * sizeof(uint4) / (best * 1e-3) / 1e9;
+    return DG_OK;
+}
+
+extern "C" dg_status degrid_measure_l2_reduce_bw(int device, double *gbs)
+{
+    using namespace dg;
+    if (!gbs || device < 0)
+        return DG_ERR_ARG;
+    *gbs = 0.0;
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
+        return DG_ERR_CUDA;
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int rows = 2048;                  // 16 MB stack: L2-resident
+    const int iters = 4096;
+    float *buf = nullptr;
+    cudaStream_t st = nullptr;
+    CUtensorMap map;
+    if (e == cudaSuccess)
+        e = cudaMalloc(&buf, sizeof(float) * (size_t)rows * kRedCols);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(buf, 0, sizeof(float) * (size_t)rows * kRedCols, st);
+    if (e == cudaSuccess)
+        e = encode_2d(&map, buf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, kRedCols, rows, sizeof(float) * kRedCols,
+                      kRedBoxW, kRedBoxH);
+    float best = 0.0f;
+    if (e == cudaSuccess)
+        best = best_of_5(st, [&] { l2_reduce_kernel<<<sms, kRedWarps * kWarp, 0, st>>>(map, rows, iters); }, &e);
+    if (st)
+        cudaStreamDestroy(st);
+    cudaFree(buf);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess || best <= 0.0f)
+        return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+    const double bytes = (double)sms * kRedWarps * iters * kRedBoxH * kRedBoxW * sizeof(float);
+    *gbs = bytes / (best * 1e-3) / 1e9;
     return DG_OK;
 }

@@ -24,7 +24,7 @@ Conventions (also used by the library):
     kernel value at grid offset (k - support/2 + 1) - f/oversample.
 
 Seeds: subgrids 0, coordinates 1, counts and list structure 2, adjoint
-visibilities 3.  Each subgrid / list draws from its own stream
+visibilities 3, the sky image of the subgrid producer 4.  Each subgrid / list draws from its own stream
 ``default_rng([seed, s])`` so that any one of them can be regenerated alone.
 """
 from __future__ import annotations
@@ -39,6 +39,7 @@ SEED_SUBGRID = 0
 SEED_UVW = 1
 SEED_STRUCTURE = 2
 SEED_ADJOINT = 3
+SEED_SKY = 4
 
 UV_SUPPORT = 8
 UV_OVERSAMPLE = 16384
@@ -350,6 +351,42 @@ def workload(name: str) -> Workload:
     if name == "scatter16_250k":
         return scattered_workload(name, [250_000] * 16)
     raise KeyError(name)
+
+
+# ---- inputs of the subgrid producer (the step upstream of degridding) -----
+
+def sky_image(n: int = 512, n_sources: int = 300, seed: int = SEED_SKY) -> np.ndarray:
+    """A model sky, complex64 [n][n] (row <-> m, column <-> l): point sources
+    of log-uniform flux in [1e-3, 1] at random pixels plus weak Gaussian
+    background, with a small imaginary part (a polarisation-like leak)."""
+    rng = np.random.default_rng(seed)
+    img = (1e-4 * rng.standard_normal((n, n)) + 1e-5j * rng.standard_normal((n, n)))
+    b = rng.integers(0, n, n_sources)
+    a = rng.integers(0, n, n_sources)
+    flux = 10.0 ** rng.uniform(-3, 0, n_sources)
+    np.add.at(img, (b, a), flux * (1 + 0.01j * rng.standard_normal(n_sources)))
+    return img.astype(np.complex64)
+
+
+def image_taper(n: int = 512) -> np.ndarray:
+    """A smooth positive image-plane correction, float32 [n][n] (an input of
+    the producer like the image: the inverse of a separable bell)."""
+    x = (np.arange(n) - n // 2) / (n / 2)
+    bell = np.cos(0.45 * np.pi * x) ** 2 + 0.05
+    return (1.0 / np.outer(bell, bell)).astype(np.float32)
+
+
+PREDICT_THETA = 0.1             # image width in direction cosines (about 5.7 degrees)
+
+
+def predict_offsets(n_subgrids: int, dw: float = 100.0):
+    """Subgrid parameters of the producer workload: every subgrid the full
+    n x n cell window (u0 = v0 = 0) of one stack of w-planes, the stacks
+    consecutive (w0_s = (s - S/2) * 4 dw, planes dw apart): int32 [S][2]
+    and float64 [S][2]."""
+    uv = np.zeros((n_subgrids, 2), dtype=np.int32)
+    w = np.stack([(np.arange(n_subgrids) - n_subgrids // 2) * 4.0 * dw, np.full(n_subgrids, dw)], axis=1)
+    return uv, np.ascontiguousarray(w, dtype=np.float64)
 
 
 # ---- inputs generated on the device ----------------------------------------

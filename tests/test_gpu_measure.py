@@ -40,3 +40,18 @@ def test_measured_l2_read_bandwidth_is_between_hbm_and_the_load_path_bound():
     assert 7000.0 < bw <= upper, (bw, upper)
     with pytest.raises(dg.DegridError):
         dg.measure_l2_read_bw(-1)
+
+
+def test_measured_l2_reduce_rate_is_plausible():
+    # the copy engines' reduce-adds of footprint tiles into an L2-resident
+    # stack: above 1 TB/s of added data (else the kernel did not keep them
+    # busy) and below what the SMs' paths to L2 could carry (128 bytes per SM
+    # per clock)
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    upper = sms * 128 * MAX_SM_MHZ * 1e6 / 1e9
+    bw = dg.measure_l2_reduce_bw(0)
+    assert 1000.0 < bw <= upper, (bw, upper)
+    with pytest.raises(dg.DegridError):
+        dg.measure_l2_reduce_bw(-1)

@@ -498,6 +498,50 @@ def test_adjoint_all_list_kinds_with_invalid_points(kind):
     assert np.all(got[1] == 0)                   # the empty subgrid stays zero
 
 
+@pytest.mark.parametrize("shape,counts,kind", [
+    ((16, 16, 4), [3000, 0, 2500, 0, 0, 800], "mixed"),     # zeroed in the kernel, empty subgrids
+    ((512, 512, 4), [40000, 0], "line"),                     # most bands untouched
+    ((40, 72, 4), [2000, 1, 0, 700], "scatter"),             # a new footprint at nearly every visibility
+    ((512, 512, 4), [300, 0, 200, 0, 0, 0, 0, 9], "line"),   # fewer items than bands: memset first
+])
+def test_adjoint_overwrites_a_dirty_output(shape, counts, kind):
+    # accumulate = 0 overwrites whatever the output held: every element is
+    # the oracle's gridding, untouched ones exactly zero (the kernel zeroes
+    # the stack band by band beside the sums, or a memset does when the call
+    # has fewer work items than bands); twice in a row, and replayed from a
+    # CUDA graph over a refilled output
+    d = dev()
+    w = small_workload(counts, kind=kind, shape=shape, seed=57)
+    y = synth.adjoint_vis(w.n_vis, seed=58)
+    ref, bad = oracle.grid(G_UV, G_W, shape, w.n_subgrids, w.uvw, w.vis_offsets, y)
+    assert bad == 0
+    yd = torch.from_numpy(y).to(d)
+    uvw = torch.from_numpy(w.uvw).to(d)
+    offs = torch.from_numpy(w.vis_offsets).to(d)
+    out = torch.full((w.n_subgrids,) + shape, float("nan"), dtype=torch.complex64, device=d)
+    zero = ref == 0
+    with dg.DegridPlan(shape=shape, device=d) as p:
+        for _ in range(2):
+            out.fill_(float("nan"))
+            got = p.grid(yd, uvw, offs, w.n_subgrids, out=out).cpu().numpy()
+            assert p.status() == 0
+            assert rel_l2(got, ref) <= TOL["c64"]
+            assert np.all(got[zero] == 0)
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream(device=d)
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                p.grid(yd, uvw, offs, w.n_subgrids, out=out)
+        for _ in range(2):
+            out.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            assert rel_l2(got, ref) <= TOL["c64"]
+            assert np.all(got[zero] == 0)
+        assert p.status() == 0
+
+
 def test_adjoint_dot_product_identity_on_gpu(plan):
     d = dev()
     w = synth.workload("line1_20k")
