@@ -58,10 +58,10 @@ constexpr int kThreads = 256;
 // as the unevaluated sum hi + lo of two floats.
 __global__ void nm1_kernel(float2 *__restrict__ nm1, int n, double dl)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)n * n)
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= n)
         return;
-    const int a = (int)(i % n), b = (int)(i / n);
+    const int i = b * n + a;
     const double l = (double)(a - n / 2) * dl, m = (double)(b - n / 2) * dl;
     const double r2 = l * l + m * m;
     if (r2 < 1.0) {
@@ -92,13 +92,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Step 1: grid (pixels / kThreads, subgrids of the pass).
+// Step 1: grid (ceil(N / kThreads), N rows, subgrids of the pass); thread
+// (a, b) of subgrid `first + z`.  32-bit index arithmetic throughout (the
+// plan keeps N * N * nz below 2^31).
 __global__ void __launch_bounds__(kThreads)
 screen_kernel(const float2 *__restrict__ image, const float *__restrict__ taper, const float2 *__restrict__ nm1,
               const double *__restrict__ w_planes, int first, int n, int nz, float2 *__restrict__ work)
 {
     __shared__ float wsplit[4];             // w0 and dw of the subgrid as (hi, lo) floats
-    const int sp = blockIdx.y, s = first + sp;
+    const int sp = blockIdx.z, s = first + sp;
     if (threadIdx.x < 2) {
         const double v = w_planes[2 * (int64_t)s + threadIdx.x];
         const float hi = (float)v;
@@ -106,11 +108,11 @@ screen_kernel(const float2 *__restrict__ image, const float *__restrict__ taper,
         wsplit[2 * threadIdx.x + 1] = (float)(v - (double)hi);
     }
     __syncthreads();
-    const int64_t np = (int64_t)n * n;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np)
+    const int a = blockIdx.x * kThreads + threadIdx.x, b = blockIdx.y;
+    if (a >= n)
         return;
-    const int a = (int)(i % n), b = (int)(i / n);
+    const int i = b * n + a;
+    const int np = n * n;
     const float2 nm = nm1[i];
     float2 cur = make_float2(0.f, 0.f), step = make_float2(1.f, 0.f);
     if (!isnan(nm.x)) {
@@ -126,22 +128,23 @@ screen_kernel(const float2 *__restrict__ image, const float *__restrict__ taper,
     }
 }
 
-// Step 3: grid (cells / kThreads, subgrids of the pass).
+// Step 3: grid (ceil(N / kThreads), N rows, subgrids of the pass).
 __global__ void __launch_bounds__(kThreads)
 window_kernel(const float2 *__restrict__ work, const int32_t *__restrict__ uv_offsets, int first, int n, int nz,
               float2 *__restrict__ sub_out)
 {
-    const int64_t np = (int64_t)n * n;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np)
+    const int sp = blockIdx.z, s = first + sp;
+    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= n)
         return;
-    const int sp = blockIdx.y, s = first + sp;
-    const int x = (int)(i % n), y = (int)(i / n);
-    const int u0 = uv_offsets[2 * (int64_t)s], v0 = uv_offsets[2 * (int64_t)s + 1];
-    const int kx = (int)((((int64_t)x + u0) % n + n) % n), ky = (int)((((int64_t)y + v0) % n + n) % n);
+    // the offsets reduced to [0, n) once (64-bit: any int32 offset)
+    const int u0 = (int)(((int64_t)uv_offsets[2 * (int64_t)s] % n + n) % n);
+    const int v0 = (int)(((int64_t)uv_offsets[2 * (int64_t)s + 1] % n + n) % n);
+    const int kx = x + u0 < n ? x + u0 : x + u0 - n, ky = y + v0 < n ? y + v0 : y + v0 - n;
     const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
-    const float2 *src = work + (int64_t)sp * nz * np + (int64_t)ky * n + kx;
-    float2 *dst = sub_out + ((int64_t)s * np + i) * nz;
+    const int np = n * n;
+    const float2 *src = work + (int64_t)sp * nz * np + ky * n + kx;
+    float2 *dst = sub_out + ((int64_t)s * np + (int64_t)y * n + x) * nz;
     if ((nz & 1) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
         for (int c = 0; c < nz; c += 2) {
             const float2 p = src[(int64_t)c * np], q = src[(int64_t)(c + 1) * np];
@@ -266,8 +269,8 @@ dg_status subgrid_predict_execute(subgrid_predict_plan_t p, void *stream, double
         return DG_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t np = (int64_t)p->n * p->n;
-    const unsigned blocks = (unsigned)((np + kThreads - 1) / kThreads);
-    nm1_kernel<<<blocks, kThreads, 0, st>>>(p->nm1, p->n, theta / p->n);
+    nm1_kernel<<<dim3((unsigned)((p->n + kThreads - 1) / kThreads), (unsigned)p->n), kThreads, 0, st>>>(
+        p->nm1, p->n, theta / p->n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return from_cuda(e);
@@ -275,17 +278,18 @@ dg_status subgrid_predict_execute(subgrid_predict_plan_t p, void *stream, double
         return DG_ERR_CUDA;
     const float2 *img = reinterpret_cast<const float2 *>(image);
     float2 *out = reinterpret_cast<float2 *>(subgrids_out);
+    const unsigned row_blocks = (unsigned)((p->n + kThreads - 1) / kThreads);
     for (int first = 0; first < n_subgrids; first += p->per_pass) {
         const int count = n_subgrids - first < p->per_pass ? n_subgrids - first : p->per_pass;
-        screen_kernel<<<dim3(blocks, count), kThreads, 0, st>>>(img, taper, p->nm1, w_planes, first, p->n, p->nz,
-                                                              p->work);
+        const dim3 grid(row_blocks, (unsigned)p->n, (unsigned)count);
+        screen_kernel<<<grid, kThreads, 0, st>>>(img, taper, p->nm1, w_planes, first, p->n, p->nz, p->work);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return from_cuda(e);
         // the whole batch (planes past `count` hold earlier passes' values and are not read)
         if (cufftExecC2C(p->fft, reinterpret_cast<cufftComplex *>(p->work), reinterpret_cast<cufftComplex *>(p->work),
                          CUFFT_FORWARD) != CUFFT_SUCCESS)
             return DG_ERR_CUDA;
-        window_kernel<<<dim3(blocks, count), kThreads, 0, st>>>(p->work, uv_offsets, first, p->n, p->nz, out);
+        window_kernel<<<grid, kThreads, 0, st>>>(p->work, uv_offsets, first, p->n, p->nz, out);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return from_cuda(e);
     }
