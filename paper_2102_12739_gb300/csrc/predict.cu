@@ -133,13 +133,17 @@ __global__ void __launch_bounds__(kThreads)
 window_kernel(const float2 *__restrict__ work, const int32_t *__restrict__ uv_offsets, int first, int n, int nz,
               float2 *__restrict__ sub_out)
 {
+    __shared__ int off[2];                  // the subgrid's cell offsets reduced to [0, n)
     const int sp = blockIdx.z, s = first + sp;
+    if (threadIdx.x < 2) {
+        const int o = uv_offsets[2 * (int64_t)s + threadIdx.x] % n;     // |o| < n: no overflow below
+        off[threadIdx.x] = o < 0 ? o + n : o;
+    }
+    __syncthreads();
     const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
     if (x >= n)
         return;
-    // the offsets reduced to [0, n) once (64-bit: any int32 offset)
-    const int u0 = (int)(((int64_t)uv_offsets[2 * (int64_t)s] % n + n) % n);
-    const int v0 = (int)(((int64_t)uv_offsets[2 * (int64_t)s + 1] % n + n) % n);
+    const int u0 = off[0], v0 = off[1];
     const int kx = x + u0 < n ? x + u0 : x + u0 - n, ky = y + v0 < n ? y + v0 : y + v0 - n;
     const float sg = ((kx + ky) & 1) ? -1.f : 1.f;
     const int np = n * n;
