@@ -17,10 +17,12 @@
 // visibilities 8k + p (pass k = 0..3) it handles.  At the end of a run the 8
 // lanes p of each row pair add their partial T through shared memory (a
 // transpose with XOR-swizzled 16-byte slots, free of bank conflicts) and lane
-// 8j + p adds column a = p of rows 2j, 2j+1 to the subgrid with 8 float2
-// atomics (c = 0..3).  Dense lists have runs of hundreds of visibilities, so
-// the atomics are a small fraction of the work.  Halves whose 32
-// visibilities share one run take a branch-free path.
+// 8j + p adds column a = p of rows 2j, 2j+1 to the subgrid: the four w
+// planes c = 0..3 of an element are 32 contiguous bytes, two 16-byte vector
+// reductions (red.global.add.v4.f32) when nz = 4 and the output is 16-byte
+// aligned, else four float2 atomics.  Dense lists have runs of hundreds of
+// visibilities, so the adds are a small fraction of the work.  Halves whose
+// 32 visibilities share one run take a branch-free path.
 #include "pipeline.cuh"
 
 namespace dg {
@@ -45,12 +47,26 @@ __device__ __forceinline__ float2 load_y(const float2 *__restrict__ vis, const B
     return lane < b.n ? __ldg(vis + b.b0 + lane) : make_float2(0.f, 0.f);
 }
 
-// T[i][a] += g_u[a] * (g_v[2j + i] * y) for the visibility in row r.
-__device__ __forceinline__ void accumulate(float2 (&T)[2][8], const RowStage &S, int r, int j, float2 y)
+// This lane's stage reads in pass 0 of a half; pass k reads row 8k + p, 8 rows
+// (16 float4 of u, 32 float2 of v) further on.  The slot swizzle of row
+// 8k + p is that of row p (bit 2 of the row is bit 2 of p).
+struct LaneRows {
+    const float4 *u0, *u1;
+    const float2 *v;
+};
+
+__device__ __forceinline__ LaneRows lane_rows(const RowStage &S, int p, int j)
 {
-    const float4 u0 = S.u[r][row_half(r, 0)];
-    const float4 u1 = S.u[r][row_half(r, 1)];
-    const float2 v = reinterpret_cast<const float2 *>(&S.v[r][row_half(r, j >> 1)])[j & 1];
+    const int sw = (p >> 2) & 1;
+    return {&S.u[p][sw], &S.u[p][sw ^ 1], reinterpret_cast<const float2 *>(&S.v[p][(j >> 1) ^ sw]) + (j & 1)};
+}
+
+// T[i][a] += g_u[a] * (g_v[2j + i] * y) for the visibility of pass k.
+__device__ __forceinline__ void accumulate(float2 (&T)[2][8], const LaneRows &L, int k, float2 y)
+{
+    const float4 u0 = L.u0[16 * k];
+    const float4 u1 = L.u1[16 * k];
+    const float2 v = L.v[32 * k];
     const float gu[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
     const float2 w0 = __fmul2_rn(y, make_float2(v.x, v.x)), w1 = __fmul2_rn(y, make_float2(v.y, v.y));
     // packed (re, im) FMAs with a duplicated real weight (bitwise two scalar FMAs)
@@ -79,17 +95,20 @@ __device__ __forceinline__ void accumulate_2d(float2 (&T)[2][8], const float *__
 
 // One visibility of a pass: the separable rows from the stage, or the 2D table.
 template <bool T2D>
-__device__ __forceinline__ void accumulate_vis(float2 (&T)[2][8], const RowStage &S,
-                                               const float *__restrict__ g2, int r, int blk, int j,
+__device__ __forceinline__ void accumulate_vis(float2 (&T)[2][8], const LaneRows &L,
+                                               const float *__restrict__ g2, int k, int blk, int j,
                                                float2 y)
 {
     if (T2D)
         accumulate_2d(T, g2, blk, j, y);
     else
-        accumulate(T, S, r, j, y);
+        accumulate(T, L, k, y);
 }
 
-// Adds the run (key, fw) to the subgrid at sub_s and clears T.
+// Adds the run (key, fw) to the subgrid at sub_s and clears T.  kVec4: every
+// element's four w planes start on a 16-byte boundary (nz = 4, so z0 = 0, and
+// an aligned output), added as two float4 reductions.
+template <bool kVec4>
 __device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *__restrict__ sub_s,
                                       int key, int fw, const Geometry &g, const float4 *wtab,
                                       const float *__restrict__ gwt, int p, int j)
@@ -101,26 +120,35 @@ __device__ __forceinline__ void flush(float2 (&T)[2][8], WarpSmem &ws, float2 *_
         T[0][a] = T[1][a] = make_float2(0.f, 0.f);
     }
     __syncwarp();
-    float4 sum = ws.t[0][j][p];
+    const float4 t0 = ws.t[0][j][p];
+    float2 s0 = make_float2(t0.x, t0.y), s1 = make_float2(t0.z, t0.w);     // T[2j][p], T[2j+1][p]
 #pragma unroll
     for (int q = 1; q < 8; ++q) {
         const float4 t = ws.t[q][j][p ^ q];
-        sum.x += t.x;
-        sum.y += t.y;
-        sum.z += t.z;
-        sum.w += t.w;
+        s0 = __fadd2_rn(s0, make_float2(t.x, t.y));
+        s1 = __fadd2_rn(s1, make_float2(t.z, t.w));
     }
     const float4 gw = wtab ? wtab[fw] : __ldg(reinterpret_cast<const float4 *>(gwt) + fw);
     float2 *e0 = sub_s + key + (int64_t)p * g.nz + (int64_t)(2 * j) * g.row_stride;
     float2 *e1 = e0 + g.row_stride;
-    atomicAdd(e0, make_float2(sum.x * gw.x, sum.y * gw.x));
-    atomicAdd(e0 + 1, make_float2(sum.x * gw.y, sum.y * gw.y));
-    atomicAdd(e0 + 2, make_float2(sum.x * gw.z, sum.y * gw.z));
-    atomicAdd(e0 + 3, make_float2(sum.x * gw.w, sum.y * gw.w));
-    atomicAdd(e1, make_float2(sum.z * gw.x, sum.w * gw.x));
-    atomicAdd(e1 + 1, make_float2(sum.z * gw.y, sum.w * gw.y));
-    atomicAdd(e1 + 2, make_float2(sum.z * gw.z, sum.w * gw.z));
-    atomicAdd(e1 + 3, make_float2(sum.z * gw.w, sum.w * gw.w));
+    const float gc[4] = {gw.x, gw.y, gw.z, gw.w};
+    if (kVec4) {
+#pragma unroll
+        for (int c = 0; c < 4; c += 2) {
+            const float2 a0 = __fmul2_rn(s0, make_float2(gc[c], gc[c]));
+            const float2 a1 = __fmul2_rn(s0, make_float2(gc[c + 1], gc[c + 1]));
+            const float2 b0 = __fmul2_rn(s1, make_float2(gc[c], gc[c]));
+            const float2 b1 = __fmul2_rn(s1, make_float2(gc[c + 1], gc[c + 1]));
+            atomicAdd(reinterpret_cast<float4 *>(e0 + c), make_float4(a0.x, a0.y, a1.x, a1.y));
+            atomicAdd(reinterpret_cast<float4 *>(e1 + c), make_float4(b0.x, b0.y, b1.x, b1.y));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            atomicAdd(e0 + c, __fmul2_rn(s0, make_float2(gc[c], gc[c])));
+            atomicAdd(e1 + c, __fmul2_rn(s1, make_float2(gc[c], gc[c])));
+        }
+    }
 }
 
 // The run state of a warp: T accumulates the run (key, fw) of subgrid s.
@@ -132,16 +160,17 @@ struct RunState {
 
 // Accumulates one half batch (32 visibilities, stage S, issued info I,
 // values y: lane i holds visibility i's) into the warp's runs.
-template <bool T2D>
+template <bool T2D, bool kVec4>
 __device__ __forceinline__ void accumulate_half(RunState &rs, WarpSmem &ws, const RowStage &S, const Issued &I,
                                                 float2 yv, const Geometry &g, const float4 *wtab,
                                                 const float *__restrict__ gwt, const float *__restrict__ g2,
                                                 int p, int j)
 {
+    const LaneRows L = lane_rows(S, p, j);
     if (I.uniform) {
         if (I.key0 != rs.key || I.fw0 != rs.fw) {
             if (rs.key >= 0)
-                flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+                flush<kVec4>(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
             rs.key = I.key0;
             rs.fw = I.fw0;
         }
@@ -151,7 +180,7 @@ __device__ __forceinline__ void accumulate_half(RunState &rs, WarpSmem &ws, cons
             float2 y;
             y.x = __shfl_sync(kFull, yv.x, r);
             y.y = __shfl_sync(kFull, yv.y, r);
-            accumulate_vis<T2D>(rs.T, S, g2, r, T2D ? __shfl_sync(kFull, I.blk, r) : 0, j, y);
+            accumulate_vis<T2D>(rs.T, L, g2, k, T2D ? __shfl_sync(kFull, I.blk, r) : 0, j, y);
         }
     } else {
         // visibilities in list order; each change of (footprint, w row)
@@ -176,19 +205,19 @@ __device__ __forceinline__ void accumulate_half(RunState &rs, WarpSmem &ws, cons
                 const int lf = __shfl_sync(kFull, fr, leader);
                 if (lk != rs.key || lf != rs.fw) {
                     if (rs.key >= 0)
-                        flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+                        flush<kVec4>(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
                     rs.key = lk;
                     rs.fw = lf;
                 }
                 const bool mine = !done && kr == lk && fr == lf;
-                accumulate_vis<T2D>(rs.T, S, g2, r, br, j, mine ? y : make_float2(0.f, 0.f));
+                accumulate_vis<T2D>(rs.T, L, g2, k, br, j, mine ? y : make_float2(0.f, 0.f));
                 done = done || mine;
             }
         }
     }
 }
 
-template <bool T2D>
+template <bool T2D, bool kVec4>
 __global__ void __launch_bounds__(kMaxWarps * kWarp, DG_ADJOINT_MIN_BLOCKS)
 adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *__restrict__ vis_in,
                const float *__restrict__ guv, const float *__restrict__ gwt, const Schedule sched,
@@ -250,19 +279,19 @@ adjoint_kernel(const Geometry g, const double *__restrict__ uvw, const float2 *_
 
         if (bA.s != rs.s) {
             if (rs.key >= 0)
-                flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+                flush<kVec4>(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
             rs.key = -1;
             rs.s = bA.s;
             rs.sub_s = sub_out + (int64_t)bA.s * g.plane;
         }
-        accumulate_half<T2D>(rs, ws, ws.st[sA][0], iA0, yA0, g, wtab, gwt, g2, p, j);
+        accumulate_half<T2D, kVec4>(rs, ws, ws.st[sA][0], iA0, yA0, g, wtab, gwt, g2, p, j);
         if (bA.n > kBatch)
-            accumulate_half<T2D>(rs, ws, ws.st[sA][1], iA1, yA1, g, wtab, gwt, g2, p, j);
+            accumulate_half<T2D, kVec4>(rs, ws, ws.st[sA][1], iA1, yA1, g, wtab, gwt, g2, p, j);
         __syncwarp();
         stage ^= 1;
     }
     if (rs.key >= 0)
-        flush(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
+        flush<kVec4>(rs.T, ws, rs.sub_s, rs.key, rs.fw, g, wtab, gwt, p, j);
 }
 
 size_t smem_bytes(const degrid_plan *p)
@@ -270,11 +299,29 @@ size_t smem_bytes(const degrid_plan *p)
     return wtable_bytes_host(p->geo) + sizeof(WarpSmem) * (size_t)p->warps_per_block;
 }
 
-// Dynamic shared memory opened so far for the plan's kernel instance on its device.
-std::atomic<size_t> &smem_record(const degrid_plan *p)
+// The kernel instance for a 2D table (or not) and vector reductions (or not).
+using AdjointKernel = decltype(&adjoint_kernel<false, false>);
+
+AdjointKernel kernel_for(const degrid_plan *p, bool vec4)
 {
-    static std::atomic<size_t> table[2][kMaxDevices];
-    return dg_smem_record(table[p->guv2 ? 1 : 0], p->device);
+    if (p->guv2)
+        return vec4 ? adjoint_kernel<true, true> : adjoint_kernel<true, false>;
+    return vec4 ? adjoint_kernel<false, true> : adjoint_kernel<false, false>;
+}
+
+// Vector reductions need every element's 32 bytes of w planes 16-byte
+// aligned: nz = kW (so z0 = 0 and every element index is a multiple of 4)
+// and a 16-byte aligned output.
+bool vec4_ok(const degrid_plan *p, const void *sub_out)
+{
+    return p->geo.nz == kW && (reinterpret_cast<uintptr_t>(sub_out) & 15u) == 0;
+}
+
+// Dynamic shared memory opened so far for the plan's kernel instance on its device.
+std::atomic<size_t> &smem_record(const degrid_plan *p, bool vec4)
+{
+    static std::atomic<size_t> table[4][kMaxDevices];
+    return dg_smem_record(table[(p->guv2 ? 2 : 0) + (vec4 ? 1 : 0)], p->device);
 }
 
 }  // namespace
@@ -288,8 +335,9 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
     (void)vis_offsets;
     Schedule sched{p->chunks, p->n_chunks, p->work_counter};
     const size_t smem = smem_bytes(p);
-    auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
-    const cudaError_t e = dg_open_smem(smem_record(p), kernel, smem);
+    const bool vec4 = vec4_ok(p, sub_out);
+    const AdjointKernel kernel = kernel_for(p, vec4);
+    const cudaError_t e = dg_open_smem(smem_record(p, vec4), kernel, smem);
     if (e != cudaSuccess)
         return e;
     return launch_pdl(kernel, dim3(grid_blocks), dim3(p->warps_per_block * kWarp), smem, st, p->geo, uvw,
@@ -297,13 +345,16 @@ cudaError_t dg_launch_adjoint(degrid_plan *p, cudaStream_t st, const double *uvw
                       sched, reinterpret_cast<float2 *>(sub_out), p->status, (const float *)p->guv2);
 }
 
+// Resident CTAs per SM of the instance an aligned output would run (both
+// instances have the same launch bounds and shared memory).
 int dg_max_blocks_per_sm_adjoint(degrid_plan *p)
 {
     using namespace dg;
     int n = 0;
     const size_t smem = smem_bytes(p);
-    auto kernel = p->guv2 ? adjoint_kernel<true> : adjoint_kernel<false>;
-    if (dg_open_smem(smem_record(p), kernel, smem) != cudaSuccess)
+    const bool vec4 = p->geo.nz == kW;
+    const AdjointKernel kernel = kernel_for(p, vec4);
+    if (dg_open_smem(smem_record(p, vec4), kernel, smem) != cudaSuccess)
         return 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, p->warps_per_block * kWarp, smem) !=
         cudaSuccess)
