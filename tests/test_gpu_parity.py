@@ -477,6 +477,32 @@ def test_adjoint_matches_oracle(plan):
         assert rel_l2(acc - 1, ref) <= TOL["c64"]
 
 
+def test_adjoint_output_off_a_16_byte_boundary():
+    # an output 8 bytes past a 16-byte boundary takes the float2 run-end adds
+    # (the aligned nz = 4 output takes 16-byte vector reductions): both give
+    # the oracle's gridding, in overwrite and in accumulate mode
+    d = dev()
+    shape = (64, 48, 4)
+    w = small_workload([1800, 0, 900], kind="mixed", shape=shape, seed=19)
+    y = torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(d)
+    uvw, offs = torch.from_numpy(w.uvw).to(d), torch.from_numpy(w.vis_offsets).to(d)
+    ref, _ = oracle.grid(G_UV, G_W, shape, w.n_subgrids, w.uvw, w.vis_offsets, synth.adjoint_vis(w.n_vis))
+    n = w.n_subgrids * int(np.prod(shape))
+    buf = torch.full((n + 1,), float("nan"), dtype=torch.complex64, device=d)
+    out = buf[1:].view((w.n_subgrids,) + shape)
+    assert out.data_ptr() % 16 == 8
+    with dg.DegridPlan(shape=shape, device=d) as p:
+        got = p.grid(y, uvw, offs, w.n_subgrids, out=out).cpu().numpy()
+        aligned = p.grid(y, uvw, offs, w.n_subgrids).cpu().numpy()
+        out.fill_(1.0)
+        acc = p.grid(y, uvw, offs, w.n_subgrids, out=out, accumulate=True).cpu().numpy()
+        assert p.status() == 0
+    assert rel_l2(got, ref) <= TOL["c64"]
+    assert rel_l2(aligned, ref) <= TOL["c64"]
+    assert rel_l2(acc - 1, ref) <= TOL["c64"]
+    assert np.all(got[ref == 0] == 0)
+
+
 @pytest.mark.parametrize("kind", ["line", "scatter", "mixed"])
 def test_adjoint_all_list_kinds_with_invalid_points(kind):
     # runs of every length (scatter: a new footprint at nearly every
