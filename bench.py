@@ -673,6 +673,7 @@ def adjoint_section(torch, dg, synth, dev, flush, steps):
         step_ms = time_fn(train_step)
         assert plan.status() == 0
     return {"workload": "diff32_100k: 32 subgrids 512x512x4, 100,000 random-line visibilities each",
+            "visibilities": w.n_vis,
             "value": w.n_vis / (call_ms[len(call_ms) // 2] * 1e-3), "unit": "gridded visibilities/s",
             "ms_per_call": call_ms[len(call_ms) // 2], "kernel_ms": kern_ms[len(kern_ms) // 2],
             "call_includes": "zeroing the 256 MB output stack, scheduling kernels, gridding kernel",
@@ -972,7 +973,11 @@ def run_ours(args, rank, world):
                                     "and for kernel loads alike"}
 
     if solo and not args.no_adjoint:
-        line["adjoint"] = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)
+        adj = adjoint_section(torch, dg, synth, dev, flush, args.aux_steps)
+        # the same 1024-flop roofline as the degridding kernel (Eq. 1's sum, transposed)
+        adj["roofline_frac"] = adj["visibilities"] * FLOP_PER_VIS / (adj["kernel_ms"] * 1e-3) / 1e12 / peak_tflops
+        adj["roofline_peak_tflops"] = peak_tflops
+        line["adjoint"] = adj
 
     if solo and not args.no_predict:
         line["predict"] = predict_section(torch, dg, synth, dev, flush, args.aux_steps, peaks["hbm_gbs"],
