@@ -232,8 +232,8 @@ dg_status degrid_plan_get_direct_runs(degrid_plan_t plan, int *min_runs);
  * counterpart for scattered coverage: each visibility's 8 x 8 x 4
  * contribution is written to shared memory and added to the stack by one
  * tensor reduce-add of the copy engine, instead of the run accumulation
- * with float2 atomics (FP32 additions in another order: the last bits
- * differ).  Needs nz = 4 and a separable G_uv table: enabling it on another
+ * with atomic adds at run ends (FP32 additions in another order: the last
+ * bits differ).  Needs nz = 4 and a separable G_uv table: enabling it on another
  * plan returns DG_ERR_UNSUPPORTED.  Calls whose stack has more than
  * 2^31 - 1 rows in all (n_subgrids * ny) take the footprint-cache kernels
  * whatever the setting (the copy engine's row coordinate is 32-bit).
@@ -382,8 +382,10 @@ dg_status degrid_plan_get_host_direct(degrid_plan_t plan, int *enabled);
  *   sub_out[s][y0+b][x0+a][z0+c] += g_uv[fv][b] g_uv[fu][a] g_w[fw][c] * vis_in[i]
  * (real weights, so the adjoint needs no conjugation).  sub_out is complex64
  * [S][ny][nx][nz] on the DEVICE, zeroed first unless accumulate != 0.
- * FP32 atomic accumulation: the summation order, and so the last bits, are
- * not deterministic.  Other arguments as for degrid_execute.  With a plan made
+ * FP32 atomic accumulation (16-byte vector reductions when nz = 4 and
+ * sub_out is 16-byte aligned, float2 atomics otherwise): the summation
+ * order, and so the last bits, are not deterministic.  Other arguments as
+ * for degrid_execute.  With a plan made
  * by degrid_plan_create_2d the weights are G[fv][fu][b][a] g_w[fw][c].
  */
 dg_status grid_adjoint_execute(degrid_plan_t plan, void *stream, int n_subgrids,
