@@ -373,9 +373,7 @@ def batched_section(torch, dg, synth, dev, flush, steps):
                 with torch.cuda.graph(graph, stream=cap):
                     plan.degrid(codes, uvw, offs, scale=scale, out=out)
             stream = torch.cuda.current_stream(dev)
-            for _ in range(3):
-                graph.replay()
-            torch.cuda.synchronize()
+            warm_up(torch, graph.replay, flush, 3, min_seconds=0.3)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(steps)]
             for a, b in ev:
@@ -450,8 +448,8 @@ def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
     for gather in (False, True):
         with dg.DegridPlan(device=dev, gather=gather) as plan:
             plan.enable_timing(steps)
-            for _ in range(3):
-                plan.grid(y, uvw, offs, w.n_subgrids, out=grid_out)
+            warm_up(torch, lambda: plan.grid(y, uvw, offs, w.n_subgrids, out=grid_out), flush, 3,
+                    min_seconds=0.3)
             for _ in range(steps):
                 flush.zero_()
                 plan.grid(y, uvw, offs, w.n_subgrids, out=grid_out)
@@ -483,9 +481,15 @@ def latency_section(torch, dg, synth, dev, steps):
     out = torch.empty(w.n_vis, dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
     with dg.DegridPlan(device=dev) as plan:
-        for _ in range(20):
+        t0 = time.perf_counter()            # clocks ramped up first (at least 0.3 s of calls)
+        done = 0
+        while done < 20 or time.perf_counter() - t0 < 0.3:
             plan.degrid(sub, uvw, offs, out=out)
+            done += 1
+            if done % 200 == 0:
+                torch.cuda.synchronize()
         torch.cuda.synchronize()
+
         def timed(prefill):
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(steps)]
@@ -564,9 +568,7 @@ def predict_section(torch, dg, synth, dev, flush, steps, hbm_gbs, plan=None, uvw
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
+        warm_up(torch, fn, flush, 3, min_seconds=0.3)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
         for a, b in ev:
@@ -617,17 +619,20 @@ def predict_section(torch, dg, synth, dev, flush, steps, hbm_gbs, plan=None, uvw
 
 
 def adjoint_section(torch, dg, synth, dev, flush, steps):
-    """Gridding (the adjoint) of 32 subgrids x 100,000 random-line visibilities."""
+    """Gridding (the adjoint) of 32 subgrids x 100,000 random-line visibilities.
+    The gridding call is timed over at least 150 L2-flushed calls (medians):
+    its kernel time varies by about 2% between groups of 50."""
     w = synth.workload("diff32_100k")
+    steps = max(steps, 150)
     uvw = torch.from_numpy(w.uvw).to(dev)
     offs = torch.from_numpy(w.vis_offsets).to(dev)
     y = torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(dev)
     out = torch.empty((w.n_subgrids,) + w.shape, dtype=torch.complex64, device=dev)
     with dg.DegridPlan(device=dev) as plan:
         plan.enable_timing(steps)
-        for _ in range(3):
-            plan.grid(y, uvw, offs, w.n_subgrids, out=out)
-        torch.cuda.synchronize()
+        # as for every timed section: clocks ramped up first (the workload's
+        # generation on the host leaves the GPU idle for about a second)
+        warm_up(torch, lambda: plan.grid(y, uvw, offs, w.n_subgrids, out=out), flush, 3, min_seconds=0.3)
         stream = torch.cuda.current_stream(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
@@ -656,9 +661,7 @@ def adjoint_section(torch, dg, synth, dev, flush, steps):
             (v - y).abs().pow(2).sum().backward()
 
         def time_fn(fn):
-            for _ in range(3):
-                fn()
-            torch.cuda.synchronize()
+            warm_up(torch, fn, flush, 3, min_seconds=0.3)
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(steps)]
             for a, b in evs:
