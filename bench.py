@@ -441,7 +441,7 @@ def scatter_section(torch, dg, synth, dev, flush, steps, l2_gbs):
                    "tuning": tuned["tuning"]}
         del codes, scale
     # gridding (the adjoint) of the same coverage: the run-accumulating kernel
-    # (float2 atomics at every run end) and the tensor reduce-add kernel
+    # (atomic adds at every run end) and the tensor reduce-add kernel
     y = torch.from_numpy(synth.adjoint_vis(w.n_vis)).to(dev)
     grid_out = torch.empty((w.n_subgrids,) + w.shape, dtype=torch.complex64, device=dev)
     gridding = {}

@@ -2,10 +2,11 @@
 //
 // The adjoint kernel (adjoint.cu) accumulates the scatter of a run of
 // visibilities that share a footprint in registers and adds it to the
-// subgrid with 256 float2 atomics when the run ends.  When consecutive
-// visibilities rarely share a footprint (sparse or short lists, the regime
-// of the paper's D2/D4 variants, Section "Results") every visibility is a
-// run of its own and the atomics bound it.  This kernel writes each
+// subgrid with 128 16-byte vector reductions (256 float2 atomics on other
+// layouts) when the run ends.  When consecutive visibilities rarely share a
+// footprint (sparse or short lists, the regime of the paper's D2/D4
+// variants, Section "Results") every visibility is a run of its own and the
+// atomics bound it.  This kernel writes each
 // visibility's whole contribution,
 //   tile[b][a][c] = g_w[c] (g_u[a] (y g_v[b]))    (the adjoint kernel's rounding),
 // into shared memory in the layout of the stack (8 rows of 32 samples) and
