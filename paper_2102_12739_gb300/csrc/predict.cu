@@ -92,39 +92,63 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// Step 1: grid (ceil(N / kThreads), N rows, subgrids of the pass); thread
-// (a, b) of subgrid `first + z`.  32-bit index arithmetic throughout (the
-// plan keeps N * N * nz below 2^31).
+// Step 1: grid (ceil(N / kThreads), N rows); thread (a, b) makes pixel (a, b)
+// of every subgrid of the pass, so the image, taper and n - 1 of the pixel
+// are read once per pass, and the plane step's screen is reused while
+// consecutive subgrids have the same plane spacing (bit for bit the value it
+// would compute again).  The subgrids' w0 and dw are split into (hi, lo)
+// floats by the block, 256 subgrids at a time.  32-bit index arithmetic
+// throughout (the plan keeps N * N * nz below 2^31).
 __global__ void __launch_bounds__(kThreads)
 screen_kernel(const float2 *__restrict__ image, const float *__restrict__ taper, const float2 *__restrict__ nm1,
-              const double *__restrict__ w_planes, int first, int n, int nz, float2 *__restrict__ work)
+              const double *__restrict__ w_planes, int first, int count, int n, int nz, float2 *__restrict__ work)
 {
-    __shared__ float wsplit[4];             // w0 and dw of the subgrid as (hi, lo) floats
-    const int sp = blockIdx.z, s = first + sp;
-    if (threadIdx.x < 2) {
-        const double v = w_planes[2 * (int64_t)s + threadIdx.x];
-        const float hi = (float)v;
-        wsplit[2 * threadIdx.x] = hi;
-        wsplit[2 * threadIdx.x + 1] = (float)(v - (double)hi);
-    }
-    __syncthreads();
+    __shared__ float4 wsplit[kThreads];     // per subgrid: (w0 hi, w0 lo, dw hi, dw lo)
     const int a = blockIdx.x * kThreads + threadIdx.x, b = blockIdx.y;
-    if (a >= n)
-        return;
-    const int i = b * n + a;
+    const bool in = a < n;
+    const int i = b * n + (in ? a : 0);
     const int np = n * n;
-    const float2 nm = nm1[i];
-    float2 cur = make_float2(0.f, 0.f), step = make_float2(1.f, 0.f);
-    if (!isnan(nm.x)) {
+    const float2 nm = in ? nm1[i] : make_float2(0.f, 0.f);
+    const bool lit = in && !isnan(nm.x);
+    float2 base = make_float2(0.f, 0.f);
+    if (lit) {
         const float2 v = image[i];
         const float t = (taper ? taper[i] : 1.f) * (((a + b) & 1) ? -1.f : 1.f);
-        cur = cmul(make_float2(v.x * t, v.y * t), screen_phasor(wsplit[0], wsplit[1], nm));
-        step = screen_phasor(wsplit[2], wsplit[3], nm);
+        base = make_float2(v.x * t, v.y * t);
     }
-    float2 *out = work + (int64_t)sp * nz * np + i;
-    for (int c = 0; c < nz; ++c) {
-        out[(int64_t)c * np] = cur;
-        cur = cmul(cur, step);
+    float2 step = make_float2(1.f, 0.f);
+    float dw_hi = 0.f, dw_lo = 0.f;
+    bool have_step = false;
+    for (int t0 = 0; t0 < count; t0 += kThreads) {
+        __syncthreads();                    // the previous tile's splits are no longer read
+        if (t0 + (int)threadIdx.x < count) {
+            const int64_t s = first + t0 + (int64_t)threadIdx.x;
+            const double w0 = w_planes[2 * s], dw = w_planes[2 * s + 1];
+            const float w0h = (float)w0, dwh = (float)dw;
+            wsplit[threadIdx.x] = make_float4(w0h, (float)(w0 - (double)w0h), dwh, (float)(dw - (double)dwh));
+        }
+        __syncthreads();
+        const int tn = count - t0 < kThreads ? count - t0 : kThreads;
+        for (int k = 0; k < tn; ++k) {
+            const float4 ws = wsplit[k];
+            float2 cur = make_float2(0.f, 0.f);
+            if (lit) {
+                cur = cmul(base, screen_phasor(ws.x, ws.y, nm));
+                if (!have_step || ws.z != dw_hi || ws.w != dw_lo) {
+                    step = screen_phasor(ws.z, ws.w, nm);
+                    dw_hi = ws.z;
+                    dw_lo = ws.w;
+                    have_step = true;
+                }
+            }
+            if (in) {
+                float2 *out = work + (int64_t)(t0 + k) * nz * np + i;
+                for (int c = 0; c < nz; ++c) {
+                    out[(int64_t)c * np] = cur;
+                    cur = cmul(cur, lit ? step : make_float2(1.f, 0.f));
+                }
+            }
+        }
     }
 }
 
@@ -286,7 +310,8 @@ dg_status subgrid_predict_execute(subgrid_predict_plan_t p, void *stream, double
     for (int first = 0; first < n_subgrids; first += p->per_pass) {
         const int count = n_subgrids - first < p->per_pass ? n_subgrids - first : p->per_pass;
         const dim3 grid(row_blocks, (unsigned)p->n, (unsigned)count);
-        screen_kernel<<<grid, kThreads, 0, st>>>(img, taper, p->nm1, w_planes, first, p->n, p->nz, p->work);
+        screen_kernel<<<dim3(row_blocks, (unsigned)p->n), kThreads, 0, st>>>(img, taper, p->nm1, w_planes, first,
+                                                                             count, p->n, p->nz, p->work);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return from_cuda(e);
         // the whole batch (planes past `count` hold earlier passes' values and are not read)
