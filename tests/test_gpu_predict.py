@@ -61,6 +61,22 @@ def test_small_stacks_every_cell(n, nz, theta, per_pass):
         assert rel_l2(got[s], ref[s]) <= TOL, (s, rel_l2(got[s], ref[s]))
 
 
+def test_passes_of_more_than_256_subgrids():
+    # a pass of 300 subgrids: the screen kernel splits the subgrids' w in
+    # tiles of 256; plane spacings equal within runs and changing between
+    # them (the step screen is reused, then made again), and a second pass
+    n, nz, S, per_pass = 16, 2, 340, 300
+    rng = np.random.default_rng(11)
+    img = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    uv = rng.integers(-40, 40, size=(S, 2)).astype(np.int32)
+    w = np.stack([rng.uniform(-3000.0, 3000.0, S), np.repeat([25.0, 40.0, 25.0, 7.5], S // 4)], axis=1)
+    got = run(img, 0.4, uv, w, nz, per_pass=per_pass)
+    ref = P.predict(img, 0.4, np.concatenate([uv, w], axis=1), nz=nz)
+    assert rel_l2(got, ref) <= TOL
+    for s in (0, 255, 256, 299, 300, S - 1):
+        assert rel_l2(got[s], ref[s]) <= TOL, s
+
+
 def test_full_size_stack_every_cell_and_a_point_source():
     # 16 subgrids of 512 x 512 x 4 from the model sky: every cell against the
     # oracle; then one unit source, against its analytic visibility
