@@ -47,8 +47,8 @@ FLOP_PER_VIS = 1024          # 256 footprint points x complex*real FMA (2 FMA = 
 TRAFFIC_KERNEL_SOURCES = ("paper_2102_12739_gb300/csrc/degrid.cu",
                           "paper_2102_12739_gb300/csrc/pipeline.cuh",
                           "paper_2102_12739_gb300/csrc/internal.cuh")
-TRAFFIC_SHA = "d5cd8f28142fceec"
-TRAFFIC_BYTES_PER_VIS = (98.469120e6 + 11.723520e6) / 4_000_000
+TRAFFIC_SHA = "a15f6785f22862b7"
+TRAFFIC_BYTES_PER_VIS = (98.424320e6 + 11.519232e6) / 4_000_000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
 # (chunk, warps per CTA, CTAs per SM, direct-arm threshold) tried on the headline workload
