@@ -117,6 +117,36 @@ def test_coords_random_and_ties_bit_exact(plan):
     assert plan.status() == bad
 
 
+def test_coords_extreme_values_on_every_axis(plan):
+    # the snap scales q by 2^k through q's exponent field: values whose
+    # exponent the add carries past the largest (into the sign bit), values
+    # at and just below 2^31 after scaling, the edges of the valid start
+    # range and the smallest denormals, each on u, v and w in turn
+    ny, nx, nz = SHAPE
+    ext = [1.7976931348623157e308, -1.7976931348623157e308, 2.0 ** 1010, 1.5 * 2.0 ** 1009, 2.0 ** 1015,
+           2.0 ** 1016, 1.9 * 2.0 ** 1016, 2.0 ** 1017, 2.0 ** 1020, -2.0 ** 1017, 2.0 ** 17, 2.0 ** 17 - 2.0 ** -15,
+           2.0 ** 24, 2.0 ** 24 - 2.0 ** -8, 2.0 ** -1074, -2.0 ** -1074, 2.0 ** -1022, 1e-310]
+    for n_ax, W, O in ((nx, 8, 16384), (ny, 8, 16384), (nz, 4, 128)):
+        top = n_ax - W // 2                         # start = n - W just below q = top - 1/2 / O
+        low = W // 2 - 1                            # start = 0 from q = low - 1/2 / O on
+        ext += [top, top - 0.5 / O, np.nextafter(top - 0.5 / O, -np.inf), top + 0.5 / O,
+                low - 0.5 / O, np.nextafter(low - 0.5 / O, np.inf), np.nextafter(low - 0.5 / O, -np.inf),
+                low + 0.0, (2.0 ** 31 - 1) / O, 2.0 ** 31 / O, (2.0 ** 31 + 1) / O]
+    ext = np.asarray(ext, dtype=np.float64)
+    base = np.array([200.25, 300.75, 2.0])
+    rows = []
+    for axis in range(3):
+        r = np.tile(base, (len(ext), 1))
+        r[:, axis] = ext
+        rows.append(r)
+    uvw = np.ascontiguousarray(np.concatenate(rows, axis=0))
+    want, bad = oracle.coords(uvw, SHAPE)
+    got = plan.coords(torch.from_numpy(uvw).to(dev())).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert plan.status() == bad
+    assert 0 < bad < len(uvw)
+
+
 def test_coords_of_full_lines_workload(plan):
     w = synth.workload("lines64_250k")
     got = plan.coords(torch.from_numpy(w.uvw).to(dev())).cpu().numpy()
